@@ -1,0 +1,160 @@
+/*
+ * fmm.h -- C ABI of the GB300 (sm_103a) recursive Strassen-Winograd SGEMM.
+ *
+ * The operation is C <- alpha * A * B + beta * C on single-precision matrices,
+ * computed by `depth` levels of Winograd's variant of Strassen's recursion
+ * (7 sub-products and 15 quadrant additions per level) over dense classical
+ * tensor-core leaves.  Background: D'Alberto, "A Heterogeneous Accelerated
+ * Matrix Multiplication: OpenCL + APU + GPU + Fast Matrix Multiply"
+ * (arXiv 1205.2927): the quadrant division of any m x n matrix is Eq. 1,
+ * the recursive C = AB / C += AB skeleton is Table 1, the leaf is an SGEMM
+ * (Sec. 3.2), and the fast recursion based on Winograd's algorithm is the
+ * optimisation named at the end of Sec. 4.3.  Throughput is reported as
+ * 2MNK / wall-clock (Sec. 4), with transfers included for host operands.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.     Row-major with leading dimensions in ELEMENTS: element (i, j)
+ *             of A is A[i * lda + j]; A is M x K, B is K x N, C is M x N.
+ *             Column-major callers compute C^T = B^T A^T by swapping A/B and
+ *             M/N.
+ * Semantics.  Netlib SGEMM: beta == 0 writes C without reading it (NaN in C
+ *             is not propagated); alpha == 0 or K == 0 reads neither A nor B
+ *             and sets C <- beta * C; M == 0 or N == 0 is a no-op.
+ * Ownership.  The caller owns A, B, C and the workspace; the library never
+ *             frees caller memory.  A plan owns only small host state.
+ * Streams.    Every device operation is enqueued on the caller's stream; no
+ *             entry point synchronises the device unless stated.
+ * Errors.     Every entry point returns a status and never aborts.  Invalid
+ *             arguments are rejected before any device work.  Kernel-side
+ *             faults that the kernels detect (a bounded wait that ran out,
+ *             an inconsistent descriptor) are recorded in a device status
+ *             word, read with fmm_get_device_status().
+ * No fallback. There is no CPU path: without a CUDA device every compute
+ *             call returns FMM_ERR_NO_DEVICE.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fmm_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID_ARG = 1,     /* null pointer, negative size, ld < row length, bad option */
+    FMM_ERR_ALIGNMENT = 2,       /* operand alignment the plan cannot handle */
+    FMM_ERR_SHAPE_MISMATCH = 3,  /* plan used with other sizes / leading dimensions */
+    FMM_ERR_OOM = 4,             /* host allocation failed */
+    FMM_ERR_CUDA = 5,            /* a CUDA runtime call failed (message: fmm_last_error()) */
+    FMM_ERR_UNSUPPORTED = 6,     /* option combination not implemented */
+    FMM_ERR_TIMEOUT = 7,         /* a bounded device wait ran out (device status word) */
+    FMM_ERR_NO_DEVICE = 8,       /* no CUDA device, or not an sm_103 device */
+    FMM_ERR_WORKSPACE = 9        /* workspace missing or smaller than required */
+} fmm_status_t;
+
+typedef enum {
+    FMM_PREC_FP32 = 0,   /* 3 x TF32: hi*hi + hi*lo + lo*hi, fp32 accumulate (FP32-class) */
+    FMM_PREC_TF32 = 1,   /* one TF32 product, fp32 accumulate */
+    FMM_PREC_BF16X3 = 2, /* bfloat16 hi/lo split, 3 products, fp32 accumulate */
+    FMM_PREC_FP16X3 = 3  /* IEEE half hi/lo split with power-of-two scaling, 3 products */
+} fmm_precision_t;
+
+typedef enum {
+    FMM_ODD_PAD = 0,  /* virtual zero padding of the bottom/right quadrants (Eq. 1) */
+    FMM_ODD_PEEL = 1  /* even core through the recursion + classical border fix-ups */
+} fmm_odd_t;
+
+typedef enum {
+    FMM_PLANNER_FIXED = 0,      /* fixed size thresholds (the paper's Table 2 style) */
+    FMM_PLANNER_EXHAUSTIVE = 1, /* time every candidate plan on the device, keep the best */
+    FMM_PLANNER_MLP = 2         /* score candidates with the registered cost-model network */
+} fmm_planner_t;
+
+typedef enum {
+    FMM_ALGO_WINOGRAD = 0,   /* 7-product Winograd recursion */
+    FMM_ALGO_CLASSICAL = 1   /* 8-product balanced quadrant recursion of Table 1 */
+} fmm_algo_t;
+
+typedef struct {
+    int depth;                 /* recursion levels; -1 = chosen by the planner */
+    int cutoff;                /* planner: smallest leaf dimension worth a level (elements) */
+    int leaf_tile;             /* leaf tile width N: 128 or 256; 0 = default */
+    fmm_precision_t precision;
+    fmm_odd_t odd;
+    fmm_planner_t planner;
+    fmm_algo_t algo;
+    int host_operands;         /* 1: A, B, C may be pinned host memory (streamed in/out) */
+    int refine_fp64;           /* reserved: residual refinement in float64 (fmm_residual) */
+} fmm_options_t;
+
+typedef struct fmm_plan_s* fmm_plan_t;
+
+/* Fill *opt with defaults: depth -1, cutoff 1024, leaf_tile 0, FP32, PAD,
+ * FIXED planner, Winograd, device operands.  Returns FMM_ERR_INVALID_ARG on NULL. */
+fmm_status_t fmm_options_default(fmm_options_t* opt);
+
+/* Build a plan for one (M, N, K, lda, ldb, ldc, options) problem.
+ *   out              receives the plan; if NULL, only *workspace_needed is set.
+ *   workspace        device memory owned by the caller, 256-byte aligned, at
+ *                    least *workspace_needed bytes; it must outlive the plan
+ *                    and must not be shared by plans running concurrently.
+ *   workspace_needed optional; receives the byte count this plan requires.
+ * The planner runs here (FMM_PLANNER_EXHAUSTIVE times candidates on `stream`
+ * and synchronises it).  Requires ld >= row length (lda >= K, ldb >= N,
+ * ldc >= N).  Errors: INVALID_ARG, WORKSPACE, UNSUPPORTED, NO_DEVICE, CUDA. */
+fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K,
+                      int64_t lda, int64_t ldb, int64_t ldc, const fmm_options_t* opt,
+                      void* workspace, size_t workspace_bytes, size_t* workspace_needed,
+                      fmm_stream_t stream);
+
+/* Run the plan: C <- alpha * A * B + beta * C.  A, B, C are device pointers,
+ * or pinned host pointers when the plan was made with host_operands = 1 (then
+ * the call streams A and B in and C out on internal copy streams ordered
+ * after `stream`, and returns once C is back in host memory).  Pageable host
+ * memory is rejected with FMM_ERR_INVALID_ARG.  Asynchronous for device
+ * operands. */
+fmm_status_t fmm_gemm(fmm_plan_t plan, float alpha, const float* A, const float* B,
+                      float beta, float* C, fmm_stream_t stream);
+
+/* Many independent products C_i <- alpha_i A_i B_i + beta_i C_i of uneven
+ * sizes in one persistent tensor-core launch.  All arrays have `count`
+ * entries and live in host memory; the matrices are device pointers.  With
+ * workspace == NULL only *workspace_needed is set.  The per-size-class plan
+ * (depth, leaf tile) follows opt->planner.  Asynchronous. */
+fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, const int64_t* K,
+                              const float* const* A, const int64_t* lda,
+                              const float* const* B, const int64_t* ldb,
+                              float* const* C, const int64_t* ldc,
+                              const float* alpha, const float* beta,
+                              const fmm_options_t* opt, void* workspace, size_t workspace_bytes,
+                              size_t* workspace_needed, fmm_stream_t stream);
+
+/* Release a plan (NULL-safe).  Never frees the caller's workspace. */
+void fmm_free(fmm_plan_t plan);
+
+/* Static string naming a status code. */
+const char* fmm_status_string(fmm_status_t s);
+
+/* Text of the last CUDA error seen by this thread's calls (static storage). */
+const char* fmm_last_error(void);
+
+/* Synchronise the plan's last stream and read its device status word:
+ * FMM_OK, or FMM_ERR_TIMEOUT when a kernel's bounded wait ran out.  The word
+ * is cleared by the read. */
+fmm_status_t fmm_get_device_status(fmm_plan_t plan);
+
+/* Plan inspection: depth, leaf tile width, precision and odd mode the plan
+ * uses (after the planner ran); any pointer may be NULL. */
+fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* precision,
+                           int* odd, int* algo);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMM_GB300_H */

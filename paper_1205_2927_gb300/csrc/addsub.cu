@@ -1,0 +1,323 @@
+// addsub.cu -- bandwidth-bound kernels of the recursion: the 8 pre-additions
+// (S1..S4 on A, T1..T4 on B) and the 7 post-additions (U1..U7) of Winograd's
+// variant of Strassen's algorithm, plus the copies the leaves need (transposed
+// right operand, aligned left operand) and C <- beta*C.
+//
+// Quadrant naming follows Eq. 1: Q0 = X11 (top-left), Q1 = X12, Q2 = X21,
+// Q3 = X22.  The right operand is kept transposed (Y = B^T, K-major) below the
+// root, so B11 = Y11^T, B12 = Y21^T, B21 = Y12^T, B22 = Y22^T and
+//   T1^T = Y21 - Y11,  T2^T = Y22 - T1^T,  T3^T = Y22 - Y21,  T4^T = T2^T - Y12.
+// Child order (one child per product P1..P7):
+//   A side: Q0, Q1, S4, Q3, S1, S2, S3        (sums only: S1, S2, S3, S4)
+//   B side: Y0, Y1, Y3, T4, T1, T2, T3        (sums only: T1, T2, T3, T4)
+// All streaming kernels move 16-byte vectors when the view allows it.
+#include "fmm_internal.h"
+
+namespace fmm {
+
+namespace {
+
+__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return f4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return f4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+// 4 consecutive elements (r, c..c+3) of quadrant q of node view `base`,
+// zero outside valid rows/cols.
+template <bool VEC>
+__device__ __forceinline__ float4 load_q(const View& v, const float* base, long long r, long long c) {
+    if (VEC) {
+        if (r < v.valid_rows && c + 3 < v.valid_cols) return __ldg(reinterpret_cast<const float4*>(base + r * v.ld + c));
+    }
+    float t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = (r < v.valid_rows && c + j < v.valid_cols) ? __ldg(base + r * v.ld + c + j) : 0.0f;
+    return f4(t[0], t[1], t[2], t[3]);
+}
+
+__device__ __forceinline__ void store4(float* p, float4 v, bool vec, long long nvalid) {
+    if (vec && nvalid >= 4) { *reinterpret_cast<float4*>(p) = v; return; }
+    if (nvalid > 0) p[0] = v.x;
+    if (nvalid > 1) p[1] = v.y;
+    if (nvalid > 2) p[2] = v.z;
+    if (nvalid > 3) p[3] = v.w;
+}
+
+// grid: x over column groups of 4, y over rows (strided), z over nodes.
+template <bool VEC, int SIDE_B, bool FULL>
+__global__ void __launch_bounds__(128) pre_add_kernel(View P, long long h, long long w, Stack out) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= w) return;
+    const long long node = blockIdx.z;
+    const float* base = P.ptr + node * P.node_stride;
+    const float* q1p = base + w;
+    const float* q2p = base + h * P.ld;
+    const float* q3p = q2p + w;
+    // quadrant views share the node's validity window, shifted
+    View v0 = P, v1 = P, v2 = P, v3 = P;
+    v1.valid_cols = P.valid_cols - w;
+    v2.valid_rows = P.valid_rows - h;
+    v3.valid_rows = P.valid_rows - h;
+    v3.valid_cols = P.valid_cols - w;
+    const long long nvalid = w - c;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        const float4 Q0 = load_q<VEC>(v0, base, r, c);
+        const float4 Q1 = load_q<VEC>(v1, q1p, r, c);
+        const float4 Q2 = load_q<VEC>(v2, q2p, r, c);
+        const float4 Q3 = load_q<VEC>(v3, q3p, r, c);
+        float4 X1, X2, X3, X4;  // S1..S4 or T1^T..T4^T
+        if (!SIDE_B) {
+            X1 = add4(Q2, Q3);   // S1 = A21 + A22
+            X2 = sub4(X1, Q0);   // S2 = S1 - A11
+            X3 = sub4(Q0, Q2);   // S3 = A11 - A21
+            X4 = sub4(Q1, X2);   // S4 = A12 - S2
+        } else {
+            X1 = sub4(Q2, Q0);   // T1^T = Y21 - Y11  (B12 - B11)
+            X2 = sub4(Q3, X1);   // T2^T = Y22 - T1^T (B22 - T1)
+            X3 = sub4(Q3, Q2);   // T3^T = Y22 - Y21  (B22 - B12)
+            X4 = sub4(X2, Q1);   // T4^T = T2^T - Y12 (T2 - B21)
+        }
+        float* o = out.ptr + (node * out.nchild) * out.child_stride + r * out.ld + c;
+        const long long cs = out.child_stride;
+        if (FULL) {
+            store4(o + 0 * cs, Q0, VEC, nvalid);
+            store4(o + 1 * cs, Q1, VEC, nvalid);
+            if (!SIDE_B) {
+                store4(o + 2 * cs, X4, VEC, nvalid);  // P3 = S4 B22
+                store4(o + 3 * cs, Q3, VEC, nvalid);  // P4 = A22 T4
+            } else {
+                store4(o + 2 * cs, Q3, VEC, nvalid);  // P3: B22
+                store4(o + 3 * cs, X4, VEC, nvalid);  // P4: T4
+            }
+            store4(o + 4 * cs, X1, VEC, nvalid);
+            store4(o + 5 * cs, X2, VEC, nvalid);
+            store4(o + 6 * cs, X3, VEC, nvalid);
+        } else {
+            store4(o + 0 * cs, X1, VEC, nvalid);
+            store4(o + 1 * cs, X2, VEC, nvalid);
+            store4(o + 2 * cs, X3, VEC, nvalid);
+            store4(o + 3 * cs, X4, VEC, nvalid);
+        }
+    }
+}
+
+// Root B side: B is K x N row-major (ldb).  Tile of 32 (k) x 32 (n) in the
+// half domain; reads the four quadrants coalesced along n, writes the
+// transposed children coalesced along k.  blockDim = (32, 8).
+template <bool FULL>
+__global__ void __launch_bounds__(256) pre_add_b_root_kernel(const float* __restrict__ B, long long ldb, long long K,
+                                                             long long N, long long kh, long long nh, Stack out) {
+    constexpr int NC = FULL ? 7 : 4;
+    __shared__ float tile[NC][32][33];
+    const long long k0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int kl = ty + 8 * i;
+        const long long k = k0 + kl, n = n0 + tx;
+        float b11 = 0.f, b12 = 0.f, b21 = 0.f, b22 = 0.f;
+        if (k < kh && n < nh) {
+            const long long kk2 = k + kh, nn2 = n + nh;
+            if (k < K && n < N) b11 = B[k * ldb + n];
+            if (k < K && nn2 < N) b12 = B[k * ldb + nn2];
+            if (kk2 < K && n < N) b21 = B[kk2 * ldb + n];
+            if (kk2 < K && nn2 < N) b22 = B[kk2 * ldb + nn2];
+        }
+        const float t1 = b12 - b11;  // T1 = B12 - B11
+        const float t2 = b22 - t1;   // T2 = B22 - T1
+        const float t3 = b22 - b12;  // T3 = B22 - B12
+        const float t4 = t2 - b21;   // T4 = T2 - B21
+        if (FULL) {
+            tile[0][kl][tx] = b11; tile[1][kl][tx] = b21; tile[2][kl][tx] = b22; tile[3][kl][tx] = t4;
+            tile[4][kl][tx] = t1;  tile[5][kl][tx] = t2;  tile[6][kl][tx] = t3;
+        } else {
+            tile[0][kl][tx] = t1; tile[1][kl][tx] = t2; tile[2][kl][tx] = t3; tile[3][kl][tx] = t4;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int nl = ty + 8 * i;
+        const long long n = n0 + nl, k = k0 + tx;
+        if (n < nh && k < kh) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) out.ptr[c * out.child_stride + n * out.ld + k] = tile[c][tx][nl];
+        }
+    }
+}
+
+// Post-additions: per node, children P1..P7 (h x w each) -> node output.
+template <bool VEC, bool ROOT>
+__global__ void __launch_bounds__(128) post_add_kernel(const float* __restrict__ P, long long ld_in, long long cs,
+                                                       long long h, long long w, float* out, long long ld_out,
+                                                       long long out_ns, long long valid_rows, long long valid_cols,
+                                                       float alpha, float beta) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= w) return;
+    const long long node = blockIdx.z;
+    const float* base = P + node * 7 * cs;
+    float* o = out + node * out_ns;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        const float* pr = base + r * ld_in + c;
+        float4 p[7];
+        if (VEC) {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) p[i] = __ldg(reinterpret_cast<const float4*>(pr + i * cs));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                float t[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) t[j] = (c + j < w) ? __ldg(pr + i * cs + j) : 0.0f;
+                p[i] = f4(t[0], t[1], t[2], t[3]);
+            }
+        }
+        const float4 U1 = add4(p[0], p[1]);   // P1 + P2
+        const float4 U2 = add4(p[0], p[5]);   // P1 + P6
+        const float4 U3 = add4(U2, p[6]);     // U2 + P7
+        const float4 U4 = add4(U2, p[4]);     // U2 + P5
+        const float4 U5 = add4(U4, p[2]);     // U4 + P3
+        const float4 U6 = sub4(U3, p[3]);     // U3 - P4
+        const float4 U7 = add4(U3, p[4]);     // U3 + P5
+        const float4 quad[4] = {U1, U5, U6, U7};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long rr = r + (q >> 1) * h;
+            const long long cc = c + (q & 1) * w;
+            float4 v = quad[q];
+            if (!ROOT) {
+                store4(o + rr * ld_out + cc, v, VEC, w - c);
+            } else {
+                if (rr >= valid_rows || cc >= valid_cols) continue;
+                const long long nv = min(min(4LL, w - c), valid_cols - cc);
+                float* dst = o + rr * ld_out + cc;
+                const bool vec = VEC && nv == 4 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0);
+                if (vec) {
+                    float4 r4 = f4(alpha * v.x, alpha * v.y, alpha * v.z, alpha * v.w);
+                    if (beta != 0.0f) {
+                        const float4 old = *reinterpret_cast<const float4*>(dst);
+                        r4.x += beta * old.x; r4.y += beta * old.y; r4.z += beta * old.z; r4.w += beta * old.w;
+                    }
+                    *reinterpret_cast<float4*>(dst) = r4;
+                } else {
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j < nv) {
+                            float x = alpha * vv[j];
+                            if (beta != 0.0f) x += beta * dst[j];
+                            dst[j] = x;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) transpose_kernel(const float* __restrict__ B, long long ldb, long long K,
+                                                        long long N, float* __restrict__ Bt, long long ldt) {
+    __shared__ float tile[32][33];
+    const long long k0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long k = k0 + ty + 8 * i, n = n0 + tx;
+        tile[ty + 8 * i][tx] = (k < K && n < N) ? B[k * ldb + n] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long n = n0 + ty + 8 * i, k = k0 + tx;
+        if (n < N && k < K) Bt[n * ldt + k] = tile[tx][ty + 8 * i];
+    }
+}
+
+__global__ void copy2d_kernel(const float* __restrict__ A, long long lda, long long M, long long K, float* dst,
+                              long long ldd) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long r = blockIdx.y; r < M; r += gridDim.y)
+        if (c < K) dst[r * ldd + c] = A[r * lda + c];
+}
+
+__global__ void scale_kernel(float* C, long long ldc, long long M, long long N, float beta) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long r = blockIdx.y; r < M; r += gridDim.y)
+        if (c < N) C[r * ldc + c] = (beta == 0.0f) ? 0.0f : beta * C[r * ldc + c];
+}
+
+inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+cudaError_t launch_pre_add(const View& parent, long long nodes, const Stack& out, int side_b, int full,
+                           cudaStream_t stream) {
+    const long long h = parent.rows / 2, w = parent.cols / 2;
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    const bool vec = aligned16(parent.ptr) && aligned16(out.ptr) && parent.ld % 4 == 0 && w % 4 == 0 &&
+                     parent.node_stride % 4 == 0 && out.ld % 4 == 0 && out.child_stride % 4 == 0;
+    dim3 grid((unsigned)((w + 4 * 128 - 1) / (4 * 128)), gy(h), (unsigned)nodes);
+#define FMM_PRE(V, S, F) pre_add_kernel<V, S, F><<<grid, 128, 0, stream>>>(parent, h, w, out)
+    if (vec) {
+        if (side_b) { if (full) FMM_PRE(true, 1, true); else FMM_PRE(true, 1, false); }
+        else        { if (full) FMM_PRE(true, 0, true); else FMM_PRE(true, 0, false); }
+    } else {
+        if (side_b) { if (full) FMM_PRE(false, 1, true); else FMM_PRE(false, 1, false); }
+        else        { if (full) FMM_PRE(false, 0, true); else FMM_PRE(false, 0, false); }
+    }
+#undef FMM_PRE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add_b_root(const float* B, long long ldb, long long K, long long N, long long kh,
+                                  long long nh, const Stack& out, int full, cudaStream_t stream) {
+    if (kh <= 0 || nh <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((nh + 31) / 32), (unsigned)((kh + 31) / 32));
+    dim3 block(32, 8);
+    if (full) pre_add_b_root_kernel<true><<<grid, block, 0, stream>>>(B, ldb, K, N, kh, nh, out);
+    else pre_add_b_root_kernel<false><<<grid, block, 0, stream>>>(B, ldb, K, N, kh, nh, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_post_add(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
+                            long long w, float* out, long long ld_out, long long out_node_stride,
+                            long long valid_rows, long long valid_cols, float alpha, float beta,
+                            cudaStream_t stream) {
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    const bool root = valid_rows >= 0;
+    const bool vec = aligned16(P) && ld_in % 4 == 0 && child_stride % 4 == 0 && w % 4 == 0 &&
+                     (root || (aligned16(out) && ld_out % 4 == 0 && out_node_stride % 4 == 0));
+    dim3 grid((unsigned)((w + 4 * 128 - 1) / (4 * 128)), gy(h), (unsigned)nodes);
+#define FMM_POST(V, R)                                                                                         \
+    post_add_kernel<V, R><<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride, \
+                                                   valid_rows, valid_cols, alpha, beta)
+    if (root) { if (vec) FMM_POST(true, true); else FMM_POST(false, true); }
+    else      { if (vec) FMM_POST(true, false); else FMM_POST(false, false); }
+#undef FMM_POST
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float* B, long long ldb, long long K, long long N, float* Bt, long long ldt,
+                             cudaStream_t stream) {
+    if (K <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32));
+    transpose_kernel<<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, Bt, ldt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d(const float* A, long long lda, long long M, long long K, float* dst, long long ldd,
+                          cudaStream_t stream) {
+    if (M <= 0 || K <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((K + 255) / 256), gy(M));
+    copy2d_kernel<<<grid, 256, 0, stream>>>(A, lda, M, K, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float* C, long long ldc, long long M, long long N, float beta, cudaStream_t stream) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((N + 255) / 256), gy(M));
+    scale_kernel<<<grid, 256, 0, stream>>>(C, ldc, M, N, beta);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm

@@ -1,0 +1,492 @@
+// fmm.cu -- C ABI, plans and the recursion scheduler.
+//
+// Schedule of one Winograd call of depth d (breadth-first: every node of a
+// level is processed by one launch per step):
+//   level 0           root pre-additions read the caller's A (row-major,
+//                     virtually zero-padded to M0 x K0) and B (transposed on
+//                     the fly) and write all 7 child operands of each side;
+//   levels 1..d-2     pre-additions write all 7 child operands per node;
+//   level d-1         pre-additions write only S1..S4 / T1..T4; the leaves read
+//                     the three plain quadrants (P1, P2, P4 / P1, P2, P3) as
+//                     strided views of the parent operands;
+//   leaves            one persistent tcgen05 launch over all 7^d products;
+//   levels d-1..0     post-additions U1..U7; the root applies alpha/beta into C.
+// The padded sizes M0, K0, N0 are multiples of 4 * 2^d so that every level
+// splits exactly (Eq. 1's ceil/floor split then has equal halves) and every
+// operand row starts on a 16-byte boundary, as the TMA tile loads require.
+// Zero padding changes no value of the product: padded rows/columns only ever
+// add exact zeros.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "../../include/fmm.h"
+#include "fmm_internal.h"
+
+using namespace fmm;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+fmm_status_t cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    return FMM_ERR_CUDA;
+}
+#define FMM_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+struct DeviceInfo {
+    int ok = 0;
+    int num_sms = 0;
+    int major = 0, minor = 0;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[64];
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+fmm_status_t device_info(DeviceInfo* out) {
+    int dev = 0;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        snprintf(g_last_error, sizeof(g_last_error), "no CUDA device");
+        return FMM_ERR_NO_DEVICE;
+    }
+    FMM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= 64) return FMM_ERR_NO_DEVICE;
+    DeviceInfo& d = g_dev[dev];
+    if (!d.ok) {
+        FMM_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+        FMM_CUDA(cudaDeviceGetAttribute(&d.major, cudaDevAttrComputeCapabilityMajor, dev));
+        FMM_CUDA(cudaDeviceGetAttribute(&d.minor, cudaDevAttrComputeCapabilityMinor, dev));
+        d.ok = 1;
+    }
+    if (!(d.major == 10 && d.minor == 3)) {
+        snprintf(g_last_error, sizeof(g_last_error), "device is sm_%d%d; this library is built for sm_103a",
+                 d.major, d.minor);
+        return FMM_ERR_NO_DEVICE;
+    }
+    if (!g_encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cuda_fail(e, "cuTensorMapEncodeTiled");
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    *out = d;
+    return FMM_OK;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline long long rup(long long x, long long a) { return (x + a - 1) / a * a; }
+inline long long ipow7(int l) { long long r = 1; while (l-- > 0) r *= 7; return r; }
+
+// 3-D K-major fp32 tile map: dims {cols, rows, batch}, box {32, box_rows, 1},
+// 128-byte swizzle, zero fill outside the dims.
+fmm_status_t encode_map(CUtensorMap* map, const float* base, long long cols, long long rows, long long batch,
+                        long long ld, long long batch_stride, int box_rows) {
+    if (cols <= 0 || rows <= 0 || batch <= 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "empty tensor map");
+        return FMM_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16 || (batch_stride * 4) % 16)
+        return FMM_ERR_ALIGNMENT;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * 4), (cuuint64_t)(batch_stride * 4)};
+    cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
+struct Level {
+    long long m, k, n;        // node operand sizes at this level
+    long long nodes;          // 7^l
+    float* achild = nullptr;  // full: 7^(l+1) child A operands; sums-only: 4 S per node
+    float* bchild = nullptr;  // same, transposed B side
+    int full = 1;
+    float* cnode = nullptr;   // node outputs (levels >= 1)
+};
+
+}  // namespace
+
+struct fmm_plan_s {
+    long long M, N, K, lda, ldb, ldc;
+    fmm_options_t opt;
+    int depth;
+    int bn;
+    int mode;                 // LeafMode
+    long long M0, K0, N0;     // padded root sizes (Winograd)
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned* status = nullptr;
+    Level lv[8];
+    float* P = nullptr;       // leaf products
+    float* Bt = nullptr;      // classical: transposed B
+    float* Acopy = nullptr;   // classical: aligned copy of A when A is not TMA-aligned
+    long long ld_bt = 0, ld_acopy = 0;
+    int num_sms = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+// Workspace carve-out.  `base` may be null (size query).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(char* b) : base(b) {}
+    template <class T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+void layout(fmm_plan_s* p, char* ws, size_t* needed) {
+    Carver cv(ws);
+    p->status = cv.take<unsigned>(64);
+    const int d = p->depth;
+    if (d == 0) {
+        p->ld_bt = rup(p->K, 4);
+        p->Bt = cv.take<float>((size_t)p->N * p->ld_bt);
+        p->ld_acopy = rup(p->K, 4);
+        const bool a_ok = (p->lda % 4) == 0;  // base alignment checked per call
+        (void)a_ok;
+        p->Acopy = cv.take<float>((size_t)p->M * p->ld_acopy);
+    } else {
+        const long long g = 4LL << d;
+        p->M0 = rup(p->M, g);
+        p->K0 = rup(p->K, g);
+        p->N0 = rup(p->N, g);
+        for (int l = 0; l <= d; ++l) {
+            p->lv[l].m = p->M0 >> l;
+            p->lv[l].k = p->K0 >> l;
+            p->lv[l].n = p->N0 >> l;
+            p->lv[l].nodes = ipow7(l);
+        }
+        for (int l = 0; l < d; ++l) {
+            Level& L = p->lv[l];
+            const Level& C = p->lv[l + 1];
+            L.full = (l < d - 1 || l == 0) ? 1 : 0;
+            const long long per = L.full ? 7 : 4;
+            L.achild = cv.take<float>((size_t)(L.nodes * per * C.m * C.k));
+            L.bchild = cv.take<float>((size_t)(L.nodes * per * C.n * C.k));
+        }
+        const Level& Lf = p->lv[d];
+        p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
+        for (int l = 1; l < d; ++l) {
+            Level& L = p->lv[l];
+            L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
+        }
+    }
+    if (needed) *needed = align_up(cv.off, 256);
+}
+
+fmm_status_t check_opts(const fmm_options_t* o) {
+    if (o->depth < -1 || o->depth > 6) return FMM_ERR_INVALID_ARG;
+    if (o->leaf_tile != 0 && o->leaf_tile != 128 && o->leaf_tile != 256) return FMM_ERR_INVALID_ARG;
+    if (o->precision < FMM_PREC_FP32 || o->precision > FMM_PREC_FP16X3) return FMM_ERR_INVALID_ARG;
+    if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL) return FMM_ERR_INVALID_ARG;
+    if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
+    if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
+    if (o->precision == FMM_PREC_BF16X3 || o->precision == FMM_PREC_FP16X3) return FMM_ERR_UNSUPPORTED;
+    if (o->odd == FMM_ODD_PEEL || o->algo == FMM_ALGO_CLASSICAL || o->host_operands) return FMM_ERR_UNSUPPORTED;
+    return FMM_OK;
+}
+
+// Fixed-threshold planner: one more level while every dimension of the next
+// level's leaves stays at or above the cut-off (the recursion point of Sec. 3.1).
+int fixed_depth(long long M, long long N, long long K, int cutoff) {
+    if (cutoff <= 0) cutoff = 1024;
+    int d = 0;
+    long long mn = M < N ? M : N;
+    if (K < mn) mn = K;
+    while (d < 4 && (mn >> (d + 1)) >= cutoff) ++d;
+    return d;
+}
+
+// Leaf launch over `groups` (already filled except tile bookkeeping).
+fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream) {
+    long long t = 0;
+    for (int g = 0; g < args.num_groups; ++g) {
+        GemmGroup& G = args.groups[g];
+        G.tiles_m = (G.M + kBM - 1) / kBM;
+        G.tiles_n = (G.N + p->bn - 1) / p->bn;
+        G.tile_begin = t;
+        t += (long long)G.tiles_m * G.tiles_n * G.batch;
+    }
+    args.total_tiles = t;
+    args.raster_m = 16;
+    args.ext_maps = nullptr;
+    args.ext_groups = nullptr;
+    args.status = p->status;
+    FMM_CUDA(launch_leaf_gemm(args, p->mode, p->bn, p->num_sms, stream));
+    return FMM_OK;
+}
+
+fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
+                           cudaStream_t stream) {
+    FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
+    const float* Aop = A;
+    long long lda = p->lda;
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
+        FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
+        Aop = p->Acopy;
+        lda = p->ld_acopy;
+    }
+    GemmArgs args;
+    memset(&args, 0, sizeof(args));
+    fmm_status_t s;
+    if ((s = encode_map(&args.maps[0], Aop, p->K, p->M, 1, lda, p->M * lda, kBM)) != FMM_OK) return s;
+    if ((s = encode_map(&args.maps[1], p->Bt, p->K, p->N, 1, p->ld_bt, p->N * p->ld_bt, p->bn)) != FMM_OK) return s;
+    GemmGroup& G = args.groups[0];
+    G.M = (int)p->M; G.N = (int)p->N; G.K = (int)p->K; G.batch = 1;
+    G.C = C; G.ldc = p->ldc; G.c_batch_stride = 0;
+    G.alpha = alpha; G.beta = beta;
+    G.map_a = 0; G.map_b = 1;
+    G.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && p->ldc % 4 == 0) ? 1 : 0;
+    args.num_groups = 1;
+    return run_leaves(p, args, stream);
+}
+
+fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
+                          cudaStream_t stream) {
+    const int d = p->depth;
+    Level* lv = p->lv;
+    // ---- level 0: root pre-additions (always all 7 children)
+    {
+        const Level& C1 = lv[1];
+        View va{A, p->lda, 0, lv[0].m, lv[0].k, p->M, p->K};
+        Stack sa{lv[0].achild, C1.k, C1.m * C1.k, 7};
+        FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
+        Stack sb{lv[0].bchild, C1.k, C1.n * C1.k, 7};
+        FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->K, p->N, C1.k, C1.n, sb, 1, stream));
+    }
+    // ---- levels 1..d-1
+    for (int l = 1; l < d; ++l) {
+        const Level& L = lv[l];
+        const Level& Ch = lv[l + 1];
+        const Level& Pa = lv[l - 1];
+        View va{Pa.achild, L.k, L.m * L.k, L.m, L.k, L.m, L.k};
+        View vb{Pa.bchild, L.k, L.n * L.k, L.n, L.k, L.n, L.k};
+        const int per = L.full ? 7 : 4;
+        Stack sa{L.achild, Ch.k, Ch.m * Ch.k, per};
+        Stack sb{L.bchild, Ch.k, Ch.n * Ch.k, per};
+        FMM_CUDA(launch_pre_add(va, L.nodes, sa, 0, L.full, stream));
+        FMM_CUDA(launch_pre_add(vb, L.nodes, sb, 1, L.full, stream));
+    }
+    // ---- leaves
+    {
+        const Level& Lf = lv[d];      // leaf sizes
+        const Level& Ll = lv[d - 1];  // last recursion level
+        GemmArgs args;
+        memset(&args, 0, sizeof(args));
+        fmm_status_t s;
+        const long long mm = Lf.m, kk = Lf.k, nn = Lf.n;
+        if (Ll.full) {
+            const long long batch = Lf.nodes;
+            if ((s = encode_map(&args.maps[0], Ll.achild, kk, mm, batch, kk, mm * kk, kBM)) != FMM_OK) return s;
+            if ((s = encode_map(&args.maps[1], Ll.bchild, kk, nn, batch, kk, nn * kk, p->bn)) != FMM_OK) return s;
+            GemmGroup& G = args.groups[0];
+            G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)batch;
+            G.C = p->P; G.ldc = nn; G.c_batch_stride = mm * nn;
+            G.alpha = 1.f; G.beta = 0.f; G.map_a = 0; G.map_b = 1; G.vec_ok = 1;
+            args.num_groups = 1;
+        } else {
+            // parent operands of the last level: stacks of Ll.nodes matrices (Ll.m x Ll.k, Ll.n x Ll.k)
+            const Level& Pa = lv[d - 2];
+            const float* pa = Pa.achild;
+            const float* pb = Pa.bchild;
+            const long long nodes = Ll.nodes;
+            const long long ka = Ll.k;  // parent row length
+            // A-side operand maps: 0..2 quadrant views Q0, Q1, Q3; 3..6 sums S1..S4
+            auto qa = [&](int qi, int qj) { return pa + qi * mm * ka + qj * kk; };
+            auto qb = [&](int qi, int qj) { return pb + qi * nn * ka + qj * kk; };
+            if ((s = encode_map(&args.maps[0], qa(0, 0), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
+            if ((s = encode_map(&args.maps[1], qa(0, 1), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
+            if ((s = encode_map(&args.maps[2], qa(1, 1), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
+            for (int j = 0; j < 4; ++j)
+                if ((s = encode_map(&args.maps[3 + j], Ll.achild + j * mm * kk, kk, mm, nodes, kk, 4 * mm * kk, kBM)) !=
+                    FMM_OK)
+                    return s;
+            // B side (transposed): 7..9 views Y0, Y1, Y3; 10..13 sums T1..T4
+            if ((s = encode_map(&args.maps[7], qb(0, 0), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+            if ((s = encode_map(&args.maps[8], qb(0, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+            if ((s = encode_map(&args.maps[9], qb(1, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+            for (int j = 0; j < 4; ++j)
+                if ((s = encode_map(&args.maps[10 + j], Ll.bchild + j * nn * kk, kk, nn, nodes, kk, 4 * nn * kk,
+                                    p->bn)) != FMM_OK)
+                    return s;
+            //                P1  P2  P3  P4  P5  P6  P7
+            const int amap[7] = {0, 1, 6, 2, 3, 4, 5};     // Q0, Q1, S4, Q3, S1, S2, S3
+            const int bmap[7] = {7, 8, 9, 13, 10, 11, 12}; // Y0, Y1, Y3, T4, T1, T2, T3
+            for (int i = 0; i < 7; ++i) {
+                GemmGroup& G = args.groups[i];
+                G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)nodes;
+                G.C = p->P + i * mm * nn; G.ldc = nn; G.c_batch_stride = 7 * mm * nn;
+                G.alpha = 1.f; G.beta = 0.f; G.map_a = amap[i]; G.map_b = bmap[i]; G.vec_ok = 1;
+            }
+            args.num_groups = 7;
+        }
+        if ((s = run_leaves(p, args, stream)) != FMM_OK) return s;
+    }
+    // ---- post-additions, bottom-up
+    for (int l = d - 1; l >= 0; --l) {
+        const Level& L = lv[l];
+        const Level& Ch = lv[l + 1];
+        const float* in = (l == d - 1) ? p->P : lv[l + 1].cnode;
+        if (l > 0) {
+            FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, L.nodes, Ch.m, Ch.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
+                                     0.f, stream));
+        } else {
+            FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, 1, Ch.m, Ch.n, C, p->ldc, 0, p->M, p->N, alpha, beta,
+                                     stream));
+        }
+    }
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm_status_t fmm_options_default(fmm_options_t* o) {
+    if (!o) return FMM_ERR_INVALID_ARG;
+    memset(o, 0, sizeof(*o));
+    o->depth = -1;
+    o->cutoff = 1024;
+    o->leaf_tile = 0;
+    o->precision = FMM_PREC_FP32;
+    o->odd = FMM_ODD_PAD;
+    o->planner = FMM_PLANNER_FIXED;
+    o->algo = FMM_ALGO_WINOGRAD;
+    o->host_operands = 0;
+    o->refine_fp64 = 0;
+    return FMM_OK;
+}
+
+const char* fmm_status_string(fmm_status_t s) {
+    switch (s) {
+        case FMM_OK: return "FMM_OK";
+        case FMM_ERR_INVALID_ARG: return "FMM_ERR_INVALID_ARG";
+        case FMM_ERR_ALIGNMENT: return "FMM_ERR_ALIGNMENT";
+        case FMM_ERR_SHAPE_MISMATCH: return "FMM_ERR_SHAPE_MISMATCH";
+        case FMM_ERR_OOM: return "FMM_ERR_OOM";
+        case FMM_ERR_CUDA: return "FMM_ERR_CUDA";
+        case FMM_ERR_UNSUPPORTED: return "FMM_ERR_UNSUPPORTED";
+        case FMM_ERR_TIMEOUT: return "FMM_ERR_TIMEOUT";
+        case FMM_ERR_NO_DEVICE: return "FMM_ERR_NO_DEVICE";
+        case FMM_ERR_WORKSPACE: return "FMM_ERR_WORKSPACE";
+    }
+    return "FMM_ERR_UNKNOWN";
+}
+
+const char* fmm_last_error(void) { return g_last_error; }
+
+fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                      const fmm_options_t* opt, void* workspace, size_t workspace_bytes, size_t* workspace_needed,
+                      fmm_stream_t stream) {
+    if (out) *out = nullptr;
+    if (M < 0 || N < 0 || K < 0) return FMM_ERR_INVALID_ARG;
+    if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return FMM_ERR_INVALID_ARG;
+    if (lda < (K > 0 ? K : 1) || ldb < (N > 0 ? N : 1) || ldc < (N > 0 ? N : 1)) return FMM_ERR_INVALID_ARG;
+    fmm_options_t o;
+    if (opt) o = *opt; else fmm_options_default(&o);
+    fmm_status_t s = check_opts(&o);
+    if (s != FMM_OK) return s;
+    fmm_plan_s tmp;
+    tmp.M = M; tmp.N = N; tmp.K = K; tmp.lda = lda; tmp.ldb = ldb; tmp.ldc = ldc;
+    tmp.opt = o;
+    tmp.depth = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
+    if (M == 0 || N == 0 || K == 0) tmp.depth = 0;
+    tmp.bn = o.leaf_tile ? o.leaf_tile : 256;
+    tmp.mode = (o.precision == FMM_PREC_TF32) ? kLeafTF32 : kLeaf3xTF32;
+    size_t need = 0;
+    layout(&tmp, nullptr, &need);
+    if (workspace_needed) *workspace_needed = need;
+    if (!out) return FMM_OK;
+    DeviceInfo di;
+    if ((s = device_info(&di)) != FMM_OK) return s;
+    if (!workspace || workspace_bytes < need) return FMM_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return FMM_ERR_ALIGNMENT;
+    fmm_plan_s* p = new (std::nothrow) fmm_plan_s(tmp);
+    if (!p) return FMM_ERR_OOM;
+    p->ws = static_cast<char*>(workspace);
+    p->ws_bytes = workspace_bytes;
+    p->num_sms = di.num_sms;
+    layout(p, p->ws, nullptr);
+    cudaError_t e = cudaMemsetAsync(p->status, 0, 64 * sizeof(unsigned), (cudaStream_t)stream);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMemsetAsync(status)"); }
+    p->last_stream = (cudaStream_t)stream;
+    *out = p;
+    return FMM_OK;
+}
+
+fmm_status_t fmm_gemm(fmm_plan_t p, float alpha, const float* A, const float* B, float beta, float* C,
+                      fmm_stream_t stream_) {
+    if (!p) return FMM_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    p->last_stream = stream;
+    if (p->M == 0 || p->N == 0) return FMM_OK;
+    if (!C) return FMM_ERR_INVALID_ARG;
+    if (alpha == 0.0f || p->K == 0) {
+        FMM_CUDA(launch_scale(C, p->ldc, p->M, p->N, beta, stream));
+        return FMM_OK;
+    }
+    if (!A || !B) return FMM_ERR_INVALID_ARG;
+    if (p->depth == 0) return run_classical(p, alpha, A, B, beta, C, stream);
+    return run_winograd(p, alpha, A, B, beta, C, stream);
+}
+
+fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, const int64_t* K, const float* const* A,
+                              const int64_t* lda, const float* const* B, const int64_t* ldb, float* const* C,
+                              const int64_t* ldc, const float* alpha, const float* beta, const fmm_options_t* opt,
+                              void* workspace, size_t workspace_bytes, size_t* workspace_needed, fmm_stream_t stream) {
+    (void)count; (void)M; (void)N; (void)K; (void)A; (void)lda; (void)B; (void)ldb; (void)C; (void)ldc;
+    (void)alpha; (void)beta; (void)opt; (void)workspace; (void)workspace_bytes; (void)workspace_needed; (void)stream;
+    return FMM_ERR_UNSUPPORTED;
+}
+
+void fmm_free(fmm_plan_t p) { delete p; }
+
+fmm_status_t fmm_get_device_status(fmm_plan_t p) {
+    if (!p) return FMM_ERR_INVALID_ARG;
+    FMM_CUDA(cudaStreamSynchronize(p->last_stream));
+    unsigned w = 0;
+    FMM_CUDA(cudaMemcpy(&w, p->status, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w) FMM_CUDA(cudaMemset(p->status, 0, sizeof(unsigned)));
+    if (w & FMM_DEV_TIMEOUT_BIT) return FMM_ERR_TIMEOUT;
+    return w ? FMM_ERR_CUDA : FMM_OK;
+}
+
+fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precision, int* odd, int* algo) {
+    if (!p) return FMM_ERR_INVALID_ARG;
+    if (depth) *depth = p->depth;
+    if (leaf_tile) *leaf_tile = p->bn;
+    if (precision) *precision = (int)p->opt.precision;
+    if (odd) *odd = (int)p->opt.odd;
+    if (algo) *algo = (int)p->opt.algo;
+    return FMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// fmm_internal.h -- structures shared by the host scheduler and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace fmm {
+
+constexpr unsigned FMM_DEV_TIMEOUT_BIT = 1u;  // device status word: a bounded wait ran out
+constexpr unsigned FMM_DEV_BADDESC_BIT = 2u;  // device status word: inconsistent descriptor
+constexpr int kMaxMaps = 16;
+constexpr int kMaxGroups = 8;
+constexpr int kBM = 128;  // leaf tile rows (one TMEM lane per row)
+constexpr int kBK = 32;   // fp32 elements per 128-byte swizzled row
+
+// One group of leaf products: `batch` independent C_b = alpha * A_b * B_b^T
+// (+ beta * C_b) sharing sizes.  A_b is M x K (K-major), B_b is N x K
+// (K-major, i.e. the transposed right operand), read through 3-D tensor maps
+// whose third coordinate is the batch index (plus an offset).
+struct GemmGroup {
+    int M, N, K;
+    int batch;
+    int tiles_m, tiles_n;
+    long long tile_begin;   // first linear tile index of this group
+    float* C;
+    long long ldc;
+    long long c_batch_stride;
+    float alpha, beta;
+    int map_a, map_b;       // tensor-map indices
+    int a_batch_off, b_batch_off;
+    int vec_ok;             // C, ldc and the batch stride allow 16-byte stores
+    int pad_;
+};
+
+struct GemmArgs {
+    CUtensorMap maps[kMaxMaps];    // used when ext_maps == nullptr
+    GemmGroup groups[kMaxGroups];  // used when ext_groups == nullptr
+    const CUtensorMap* ext_maps;   // device-memory tables (batched launches)
+    const GemmGroup* ext_groups;
+    int num_groups;
+    int raster_m;                  // tile rows per raster band
+    long long total_tiles;
+    unsigned* status;              // device status word
+};
+
+// precision of a leaf launch
+enum LeafMode : int { kLeafTF32 = 0, kLeaf3xTF32 = 1 };
+
+// Launch the persistent tensor-core leaf kernel.  Returns a cudaError_t.
+cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms, cudaStream_t stream);
+size_t leaf_smem_bytes(int mode, int bn);
+
+// ------------------------------------------------------------ additions
+// A matrix operand view: `nodes` matrices of rows x cols, node i at
+// ptr + i * node_stride, row stride ld (elements).  Reads outside
+// valid_rows x valid_cols are zero (virtual padding of the root).
+struct View {
+    const float* ptr;
+    long long ld;
+    long long node_stride;
+    long long rows, cols;
+    long long valid_rows, valid_cols;
+};
+// Output stack of children: child c of node p is at
+// ptr + (p * nchild + c) * child_stride, row stride ld.
+struct Stack {
+    float* ptr;
+    long long ld;
+    long long child_stride;
+    int nchild;
+};
+
+// Pre-additions of one level, A side (S1..S4) or transposed-B side (T1..T4
+// transposed).  full = 1 writes all 7 child operands (quadrant copies
+// included); full = 0 writes only the 4 sums.
+cudaError_t launch_pre_add(const View& parent, long long nodes, const Stack& out, int side_b, int full,
+                           cudaStream_t stream);
+// Root B side: reads row-major B (K x N) and writes transposed children.
+cudaError_t launch_pre_add_b_root(const float* B, long long ldb, long long K, long long N, long long kh,
+                                  long long nh, const Stack& out, int full, cudaStream_t stream);
+// Post-additions of one level: children outputs (stack of 7 per node, each h x w,
+// row stride ld_in) -> node outputs (2h x 2w).  At the root: C = alpha*U + beta*C
+// restricted to valid rows/cols.
+cudaError_t launch_post_add(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
+                            long long w, float* out, long long ld_out, long long out_node_stride,
+                            long long valid_rows, long long valid_cols, float alpha, float beta,
+                            cudaStream_t stream);
+// Transposed copy: B (K x N, ldb) -> Bt (N x K, ldt).
+cudaError_t launch_transpose(const float* B, long long ldb, long long K, long long N, float* Bt, long long ldt,
+                             cudaStream_t stream);
+// Plain copy of an M x K matrix into a buffer with another leading dimension.
+cudaError_t launch_copy2d(const float* A, long long lda, long long M, long long K, float* dst, long long ldd,
+                          cudaStream_t stream);
+// C <- beta * C (beta == 0 writes zeros).
+cudaError_t launch_scale(float* C, long long ldc, long long M, long long N, float beta, cudaStream_t stream);
+
+}  // namespace fmm

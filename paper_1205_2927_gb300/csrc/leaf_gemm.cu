@@ -1,0 +1,304 @@
+// leaf_gemm.cu -- persistent, warp-specialised tcgen05 leaf GEMM for sm_103a.
+//
+// Computes, for every group g and batch entry b of a launch,
+//     C_b = alpha * A_b * B_b^T + beta * C_b      (A_b: M x K, B_b: N x K, both K-major)
+// i.e. the dense classical leaf products of the recursion (the SGEMM leaf of
+// Sec. 3.2; c_ij = sum_k a_ik b_kj, Sec. 3.3), all leaves of one level in a
+// single launch.
+//
+// Pipeline per CTA (one CTA per SM, 1 tile of 128 x BN outputs at a time):
+//   warp 0        TMA producer: A and B tiles (128 x 32 and BN x 32 fp32,
+//                 128-byte swizzle) into a ring of shared-memory stages
+//   warp 1        MMA issuer: tcgen05.mma kind::tf32 (M = 128, N = BN, K = 8)
+//                 into a double-buffered TMEM accumulator (2 x BN columns)
+//   warp 2        TMEM allocation / release
+//   warps 4..7    epilogue: tcgen05.ld -> alpha/beta -> global stores
+//   warps 8..11   (3xTF32 only) split each landed stage in place into
+//                 hi = tf32(x) and a lo = tf32(x - hi) copy, so that the MMA
+//                 warp issues lo*hi + hi*lo + hi*hi with fp32 accumulation.
+// Every mbarrier wait is bounded (ptx.cuh): a broken pipeline records a
+// timeout in the status word and the kernel returns.
+#include "fmm_internal.h"
+#include "ptx.cuh"
+
+namespace fmm {
+
+template <int BN, int MODE>
+struct LeafCfg {
+    static constexpr int kStages = (MODE == kLeafTF32) ? (BN == 256 ? 4 : 6) : (BN == 256 ? 2 : 3);
+    static constexpr int kABytes = kBM * 128;
+    static constexpr int kBBytes = BN * 128;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kLoBytes = (MODE == kLeaf3xTF32) ? kStageBytes : 0;
+    static constexpr int kTmemCols = 2 * BN;
+    static constexpr int kThreads = (MODE == kLeaf3xTF32) ? 384 : 256;
+    static constexpr int kBarBytes = 256;
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * (kStageBytes + kLoBytes) + kBarBytes;
+    static_assert((3 * kStages + 4) * 8 + 16 <= kBarBytes, "barrier area");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+    static_assert(kTmemCols == 256 || kTmemCols == 512, "TMEM columns");
+};
+
+__device__ __forceinline__ void decode_tile(const GemmGroup* groups, int ng, int raster_m, long long t, int& g,
+                                            int& b, int& tm, int& tn) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (groups[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    g = lo;
+    const GemmGroup& G = groups[g];
+    const long long local = t - G.tile_begin;
+    const long long per = (long long)G.tiles_m * G.tiles_n;
+    b = (int)(local / per);
+    const int r = (int)(local - (long long)b * per);
+    const int band = raster_m * G.tiles_n;
+    const int sr = r / band;
+    const int rr = r - sr * band;
+    const int gm = min(raster_m, G.tiles_m - sr * raster_m);
+    tn = rr / gm;
+    tm = sr * raster_m + (rr - tn * gm);
+}
+
+template <int BN, int MODE>
+__global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kernel(const __grid_constant__ GemmArgs args) {
+    using Cfg = LeafCfg<BN, MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    const uint32_t base = (raw_addr + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw_addr);
+    const uint32_t stage0 = base;                                       // raw stages
+    const uint32_t lo0 = base + Cfg::kStages * Cfg::kStageBytes;        // lo copies (3xTF32)
+    const uint32_t bar0 = lo0 + Cfg::kStages * Cfg::kLoBytes;
+    uint8_t* bar_ptr = base_ptr + (bar0 - base);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 8 * (3 * Cfg::kStages + 4));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar_ptr + 8 * (3 * Cfg::kStages + 4) + 8);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (Cfg::kStages + s); };
+    auto ready_bar = [&](int s) { return bar0 + 8u * (2 * Cfg::kStages + s); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (3 * Cfg::kStages + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (3 * Cfg::kStages + 2 + a); };
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const CUtensorMap* maps = args.ext_maps ? args.ext_maps : args.maps;
+    const GemmGroup* groups = args.ext_groups ? args.ext_groups : args.groups;
+    const int ng = args.num_groups;
+    const long long total = args.total_tiles;
+    unsigned* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::kStages; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+            mbar_init(ready_bar(s), 128);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 128);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) {
+        tmem_alloc(smem_u32(tmem_slot), Cfg::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int g, b, tm, tn;
+                decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+                const GemmGroup& G = groups[g];
+                const CUtensorMap* ma = maps + G.map_a;
+                const CUtensorMap* mb = maps + G.map_b;
+                const int nk = (G.K + kBK - 1) / kBK;
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                    mbar_arrive_expect_tx(full_bar(stage), Cfg::kStageBytes);
+                    const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
+                    tma_load_3d(sa, ma, full_bar(stage), kb * kBK, tm * kBM, b + G.a_batch_off);
+                    tma_load_3d(sa + Cfg::kABytes, mb, full_bar(stage), kb * kBK, tn * BN, b + G.b_batch_off);
+                    if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = make_idesc(2u, kBM, BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int g, b, tm, tn;
+                decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+                const int nk = (groups[g].K + kBK - 1) / kBK;
+                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < nk; ++kb) {
+                    const uint32_t wb = (MODE == kLeaf3xTF32) ? ready_bar(stage) : full_bar(stage);
+                    if (!mbar_wait(wb, phase, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
+                    const uint32_t sb = sa + Cfg::kABytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = sdesc_kmajor_sw128(sa + kk * 32);
+                        const uint64_t bd = sdesc_kmajor_sw128(sb + kk * 32);
+                        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                        if constexpr (MODE == kLeaf3xTF32) {
+                            const uint32_t la = lo0 + stage * Cfg::kStageBytes;
+                            const uint64_t ald = sdesc_kmajor_sw128(la + kk * 32);
+                            const uint64_t bld = sdesc_kmajor_sw128(la + Cfg::kABytes + kk * 32);
+                            mma_tf32(d, ald, bd, idesc, first);  // lo_a * hi_b
+                            mma_tf32(d, ad, bld, idesc, 1u);     // hi_a * lo_b
+                            mma_tf32(d, ad, bd, idesc, 1u);      // hi_a * hi_b
+                        } else {
+                            mma_tf32(d, ad, bd, idesc, first);
+                        }
+                    }
+                    mma_commit(empty_bar(stage));
+                    if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(acc));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+            int g, b, tm, tn;
+            decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+            const GemmGroup& G = groups[g];
+            bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int row = tm * kBM + q * 32 + lane;
+            const bool row_ok = row < G.M;
+            float* crow = G.C + (long long)b * G.c_batch_stride + (long long)(row_ok ? row : 0) * G.ldc;
+            const float alpha = G.alpha, beta = G.beta;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
+                tmem_ld_wait();
+                const int col0 = tn * BN + c * 32;
+                if (row_ok && col0 < G.N) {
+                    float* cp = crow + col0;
+                    if (G.vec_ok && col0 + 32 <= G.N) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            float4 v;
+                            v.x = alpha * __uint_as_float(r[j + 0]);
+                            v.y = alpha * __uint_as_float(r[j + 1]);
+                            v.z = alpha * __uint_as_float(r[j + 2]);
+                            v.w = alpha * __uint_as_float(r[j + 3]);
+                            if (beta != 0.0f) {
+                                const float4 o = *reinterpret_cast<const float4*>(cp + j);
+                                v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                            }
+                            *reinterpret_cast<float4*>(cp + j) = v;
+                        }
+                    } else {
+                        const int lim = min(32, G.N - col0);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j < lim) {
+                                float v = alpha * __uint_as_float(r[j]);
+                                if (beta != 0.0f) v += beta * cp[j];
+                                cp[j] = v;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty_bar(acc));
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    } else if (MODE == kLeaf3xTF32 && warp >= 8) {
+        // ------------------------------------------------ hi/lo split
+        const int tid = threadIdx.x - 256;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            int g, b, tm, tn;
+            decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+            const int nk = (groups[g].K + kBK - 1) / kBK;
+            for (int kb = 0; kb < nk; ++kb) {
+                bool w = mbar_wait(full_bar(stage), phase, abort_flag, status);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                float4* src = reinterpret_cast<float4*>(base_ptr + stage * Cfg::kStageBytes);
+                float4* dst = reinterpret_cast<float4*>(base_ptr + (lo0 - base) + stage * Cfg::kStageBytes);
+#pragma unroll 4
+                for (int i = tid; i < Cfg::kStageBytes / 16; i += 128) {
+                    const float4 v = src[i];
+                    float4 h, l;
+                    h.x = tf32_round_rne(v.x); l.x = tf32_round_rne(v.x - h.x);
+                    h.y = tf32_round_rne(v.y); l.y = tf32_round_rne(v.y - h.y);
+                    h.z = tf32_round_rne(v.z); l.z = tf32_round_rne(v.z - h.z);
+                    h.w = tf32_round_rne(v.w); l.w = tf32_round_rne(v.w - h.w);
+                    src[i] = h;
+                    dst[i] = l;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(ready_bar(stage));
+                if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+            }
+        }
+    }
+
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+template <int BN, int MODE>
+static cudaError_t launch_impl(const GemmArgs& args, int num_sms, cudaStream_t stream) {
+    using Cfg = LeafCfg<BN, MODE>;
+    auto kern = leaf_gemm_kernel<BN, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    if (e != cudaSuccess) return e;
+    if (args.total_tiles <= 0) return cudaSuccess;
+    const long long grid = args.total_tiles < num_sms ? args.total_tiles : num_sms;
+    kern<<<(unsigned)grid, Cfg::kThreads, Cfg::kSmem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+size_t leaf_smem_bytes(int mode, int bn) {
+    if (mode == kLeafTF32) return bn == 256 ? LeafCfg<256, kLeafTF32>::kSmem : LeafCfg<128, kLeafTF32>::kSmem;
+    return bn == 256 ? LeafCfg<256, kLeaf3xTF32>::kSmem : LeafCfg<128, kLeaf3xTF32>::kSmem;
+}
+
+cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms, cudaStream_t stream) {
+    if (mode == kLeafTF32) {
+        return bn == 256 ? launch_impl<256, kLeafTF32>(args, num_sms, stream)
+                         : launch_impl<128, kLeafTF32>(args, num_sms, stream);
+    }
+    return bn == 256 ? launch_impl<256, kLeaf3xTF32>(args, num_sms, stream)
+                     : launch_impl<128, kLeaf3xTF32>(args, num_sms, stream);
+}
+
+}  // namespace fmm

@@ -1,0 +1,193 @@
+"""Thin ctypes binding over ``libfmm_gb300.so`` (the C ABI declared in include/fmm.h).
+
+Argument marshalling only: every step of the multiply runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the workspace, and the operand
+tensors a caller passes in) and the current CUDA stream.  Importing this
+module loads the library and raises if it has not been built: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+FMM_OK = 0
+STATUS_NAMES = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_ALIGNMENT", 3: "FMM_ERR_SHAPE_MISMATCH",
+                4: "FMM_ERR_OOM", 5: "FMM_ERR_CUDA", 6: "FMM_ERR_UNSUPPORTED", 7: "FMM_ERR_TIMEOUT",
+                8: "FMM_ERR_NO_DEVICE", 9: "FMM_ERR_WORKSPACE"}
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16x3": 2, "fp16x3": 3}
+ODD = {"pad": 0, "peel": 1}
+PLANNERS = {"fixed": 0, "exhaustive": 1, "mlp": 2}
+ALGOS = {"winograd": 0, "classical": 1}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        try:
+            detail = _lib.fmm_last_error().decode()
+            if detail:
+                msg += f" ({detail})"
+        except Exception:
+            pass
+        super().__init__(msg)
+
+
+class Options(C.Structure):
+    _fields_ = [("depth", C.c_int), ("cutoff", C.c_int), ("leaf_tile", C.c_int), ("precision", C.c_int),
+                ("odd", C.c_int), ("planner", C.c_int), ("algo", C.c_int), ("host_operands", C.c_int),
+                ("refine_fp64", C.c_int)]
+
+
+def _load():
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -m paper_1205_2927_gb300.build)")
+    lib = C.CDLL(path)
+    i64, vp, sz = C.c_int64, C.c_void_p, C.c_size_t
+    lib.fmm_options_default.argtypes = [C.POINTER(Options)]
+    lib.fmm_options_default.restype = C.c_int
+    lib.fmm_plan.argtypes = [C.POINTER(vp), i64, i64, i64, i64, i64, i64, C.POINTER(Options), vp, sz,
+                             C.POINTER(sz), vp]
+    lib.fmm_plan.restype = C.c_int
+    lib.fmm_gemm.argtypes = [vp, C.c_float, vp, vp, C.c_float, vp, vp]
+    lib.fmm_gemm.restype = C.c_int
+    lib.fmm_gemm_batched.argtypes = [C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(vp),
+                                     C.POINTER(i64), C.POINTER(vp), C.POINTER(i64), C.POINTER(vp),
+                                     C.POINTER(i64), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                     C.POINTER(Options), vp, sz, C.POINTER(sz), vp]
+    lib.fmm_gemm_batched.restype = C.c_int
+    lib.fmm_free.argtypes = [vp]
+    lib.fmm_free.restype = None
+    lib.fmm_status_string.argtypes = [C.c_int]
+    lib.fmm_status_string.restype = C.c_char_p
+    lib.fmm_last_error.argtypes = []
+    lib.fmm_last_error.restype = C.c_char_p
+    lib.fmm_get_device_status.argtypes = [vp]
+    lib.fmm_get_device_status.restype = C.c_int
+    lib.fmm_plan_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 5
+    lib.fmm_plan_info.restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def _check(status, where):
+    if status != FMM_OK:
+        raise FmmError(status, where)
+
+
+def options(depth=-1, cutoff=1024, leaf_tile=0, precision="fp32", odd="pad", planner="fixed",
+            algo="winograd", host_operands=0, refine_fp64=0) -> Options:
+    o = Options()
+    _check(_lib.fmm_options_default(C.byref(o)), "fmm_options_default")
+    o.depth, o.cutoff, o.leaf_tile = depth, cutoff, leaf_tile
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.odd = ODD[odd] if isinstance(odd, str) else int(odd)
+    o.planner = PLANNERS[planner] if isinstance(planner, str) else int(planner)
+    o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    o.host_operands, o.refine_fp64 = host_operands, refine_fp64
+    return o
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ same names as the C ABI
+
+def fmm_plan(M, N, K, lda, ldb, ldc, opt=None, workspace=None, workspace_bytes=0, stream=None, query_only=False):
+    """Returns (plan_handle or None, workspace_needed)."""
+    need = C.c_size_t(0)
+    if query_only:
+        _check(_lib.fmm_plan(None, M, N, K, lda, ldb, ldc, C.byref(opt) if opt else None, None, 0,
+                             C.byref(need), None), "fmm_plan(query)")
+        return None, need.value
+    h = C.c_void_p()
+    _check(_lib.fmm_plan(C.byref(h), M, N, K, lda, ldb, ldc, C.byref(opt) if opt else None,
+                         C.c_void_p(workspace), workspace_bytes, C.byref(need), _stream_ptr(stream)),
+           "fmm_plan")
+    return h, need.value
+
+
+def fmm_gemm(plan, alpha, A_ptr, B_ptr, beta, C_ptr, stream=None):
+    _check(_lib.fmm_gemm(plan, C.c_float(alpha), C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_float(beta),
+                         C.c_void_p(C_ptr), _stream_ptr(stream)), "fmm_gemm")
+
+
+def fmm_free(plan):
+    _lib.fmm_free(plan)
+
+
+def fmm_get_device_status(plan):
+    return _lib.fmm_get_device_status(plan)
+
+
+def fmm_plan_info(plan):
+    vals = [C.c_int() for _ in range(5)]
+    _check(_lib.fmm_plan_info(plan, *[C.byref(v) for v in vals]), "fmm_plan_info")
+    return dict(zip(("depth", "leaf_tile", "precision", "odd", "algo"), [v.value for v in vals]))
+
+
+# ------------------------------------------------------------------ convenience over torch tensors
+
+class Plan:
+    """A plan plus the workspace it owns (a torch uint8 device tensor)."""
+
+    def __init__(self, M, N, K, lda=None, ldb=None, ldc=None, device=None, stream=None, **opt_kwargs):
+        import torch
+        self.M, self.N, self.K = int(M), int(N), int(K)
+        self.lda = int(lda if lda is not None else max(K, 1))
+        self.ldb = int(ldb if ldb is not None else max(N, 1))
+        self.ldc = int(ldc if ldc is not None else max(N, 1))
+        self.opt = options(**opt_kwargs)
+        _, need = fmm_plan(self.M, self.N, self.K, self.lda, self.ldb, self.ldc, self.opt, query_only=True)
+        self.workspace_bytes = need
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+        self.handle, _ = fmm_plan(self.M, self.N, self.K, self.lda, self.ldb, self.ldc, self.opt,
+                                  self.workspace.data_ptr(), self.workspace.numel(), stream)
+        self.info = fmm_plan_info(self.handle)
+
+    def __call__(self, A, B, C=None, alpha=1.0, beta=0.0, stream=None):
+        import torch
+        if C is None:
+            C = torch.empty((self.M, self.ldc), dtype=torch.float32, device=A.device)[:, : self.N]
+        for t in (A, B, C):
+            assert t.dtype == torch.float32 and t.is_cuda
+        fmm_gemm(self.handle, alpha, A.data_ptr(), B.data_ptr(), beta, C.data_ptr(), stream)
+        return C
+
+    def device_status(self):
+        return fmm_get_device_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmm_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def matmul(A, B, depth=-1, precision="fp32", **kw):
+    """C = A @ B for contiguous float32 CUDA tensors via a one-off plan."""
+    M, K = A.shape
+    N = B.shape[1]
+    p = Plan(M, N, K, A.stride(0), B.stride(0), N, depth=depth, precision=precision, **kw)
+    return p(A, B)

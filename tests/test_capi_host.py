@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every function include/fmm.h declares, validates arguments before touching a
+device, sizes workspaces, and refuses to compute without a GPU (no CPU path)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1205_2927_gb300 import build
+    build.build()
+    from paper_1205_2927_gb300 import fmm
+    return fmm
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(fmm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(F):
+    names = declared_functions()
+    assert "fmm_plan" in names and "fmm_gemm" in names and "fmm_gemm_batched" in names and "fmm_free" in names
+    lib = C.CDLL(F._build.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_options_default(F):
+    o = F.options()
+    assert (o.depth, o.cutoff, o.leaf_tile, o.precision, o.odd, o.planner, o.algo) == (-1, 1024, 0, 0, 0, 0, 0)
+
+
+def test_status_strings(F):
+    lib = F.library()
+    for code, name in F.STATUS_NAMES.items():
+        assert lib.fmm_status_string(code).decode() == name
+
+
+def _query(F, M, N, K, **kw):
+    return F.fmm_plan(M, N, K, max(K, 1), max(N, 1), max(N, 1), F.options(**kw), query_only=True)[1]
+
+
+def test_workspace_query_grows_with_depth(F):
+    n = 4096
+    sizes = [_query(F, n, n, n, depth=d) for d in range(5)]
+    assert all(s > 0 and s % 256 == 0 for s in sizes)
+    assert sizes[1] < sizes[2] < sizes[3] < sizes[4]
+    # depth 1: 7 child operands per side (n/2)^2 each, 7 products (n/2)^2
+    q = (n // 2) ** 2 * 4
+    assert sizes[1] >= 21 * q
+
+
+def test_workspace_query_pads_to_level_granule(F):
+    # 1000 at depth 2 pads to a multiple of 16: 1008
+    s = _query(F, 1000, 1000, 1000, depth=2)
+    s_exact = _query(F, 1008, 1008, 1008, depth=2)
+    assert s == s_exact
+
+
+@pytest.mark.parametrize("args", [
+    (-1, 4, 4, 4, 4, 4), (4, 4, 4, 3, 4, 4), (4, 4, 4, 4, 3, 4), (4, 4, 4, 4, 4, 3),
+])
+def test_invalid_sizes_rejected(F, args):
+    need = C.c_size_t(0)
+    st = F.library().fmm_plan(None, *args, None, None, 0, C.byref(need), None)
+    assert st == 1  # FMM_ERR_INVALID_ARG
+
+
+def test_invalid_options_rejected(F):
+    need = C.c_size_t(0)
+    lib = F.library()
+    for kw in ({"leaf_tile": 64}, {"depth": 9}, {"precision": 7}):
+        o = F.options(**kw)
+        assert lib.fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 1
+
+
+def test_gemm_rejects_null_plan(F):
+    assert F.library().fmm_gemm(None, C.c_float(1), None, None, C.c_float(0), None, None) == 1
+    F.library().fmm_free(None)  # NULL-safe
+
+
+def test_no_cpu_fallback_without_gpu(F):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    need = C.c_size_t(0)
+    o = F.options(depth=0)
+    st = F.library().fmm_plan(C.byref(h), 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None)
+    assert st == 8  # FMM_ERR_NO_DEVICE
+    assert not h.value

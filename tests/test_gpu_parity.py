@@ -1,0 +1,160 @@
+"""GPU parity of the C-ABI path against the CPU oracle.
+
+Bit-exact where every partial sum is an exact integer below 2^24 (small-integer
+operands); otherwise within the max-norm bound
+||C - C64||_max / (||A||_max ||B||_max K) <= 2e-6 for the FP32 (3xTF32) path at
+depth <= 3.  All calls go through fmm_plan / fmm_gemm.
+"""
+import numpy as np
+import pytest
+
+import oracle.fmm_oracle as O
+from paper_1205_2927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP32_BOUND = 2e-6
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    import torch  # noqa: F401
+    from paper_1205_2927_gb300 import fmm as F
+    return F
+
+
+def run(fmm, A, B, C0=None, alpha=1.0, beta=0.0, **kw):
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    dC = torch.from_numpy(np.ascontiguousarray(C0)).cuda() if C0 is not None else torch.empty((M, N), device="cuda")
+    plan = fmm.Plan(M, N, K, **kw)
+    plan(dA, dB, dC, alpha=alpha, beta=beta)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    info = plan.info
+    plan.close()
+    return dC.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+@pytest.mark.parametrize("m,k,n", [(128, 32, 256), (256, 256, 256), (200, 100, 300), (777, 333, 515), (1, 1, 1)])
+@pytest.mark.parametrize("bn", [128, 256])
+def test_classical_bit_exact_small_int(fmm, prec, m, k, n, bn):
+    A = I.small_int((m, k), 1000 + m, r=3)
+    B = I.small_int((k, n), 2000 + n, r=3)
+    C, info = run(fmm, A, B, depth=0, precision=prec, leaf_tile=bn)
+    assert info["depth"] == 0
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64))
+    assert np.array_equal(C, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("m,k,n", [(512, 512, 512), (300, 200, 260), (1024, 640, 768)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_winograd_bit_exact_small_int(fmm, m, k, n, d):
+    A = I.small_int((m, k), 3000 + m + d, r=2)
+    B = I.small_int((k, n), 4000 + n + d, r=2)
+    C, info = run(fmm, A, B, depth=d, precision="fp32")
+    assert info["depth"] == d
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64))
+    # the fp32 oracle recursion is exact here too: both equal the integer product
+    assert np.array_equal(O.winograd(A, B, d, "pad"), ref.astype(np.float32))
+    assert np.array_equal(C, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal"])
+@pytest.mark.parametrize("d", [0, 1, 2, 3])
+def test_fp32_error_bound(fmm, dist, d):
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(1, d), dist)
+    C, _ = run(fmm, A, B, depth=d, precision="fp32")
+    err = O.error_metric(C, O.classical(A, B), A, B)
+    assert err <= FP32_BOUND, err
+
+
+def test_tf32_is_coarser_than_fp32(fmm):
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(1, 7))
+    ref = O.classical(A, B)
+    e32 = O.error_metric(run(fmm, A, B, depth=0, precision="fp32")[0], ref, A, B)
+    etf = O.error_metric(run(fmm, A, B, depth=0, precision="tf32")[0], ref, A, B)
+    assert e32 < etf / 20, (e32, etf)
+
+
+def test_fp32_matches_three_product_split_model(fmm):
+    # the 3xTF32 leaf equals hi*hi + hi*lo + lo*hi (round-to-nearest splits)
+    # up to fp32 accumulation error, far tighter than the error bound
+    m, k, n = 256, 512, 256
+    A, B = I.operands(m, k, n, 77)
+    C, _ = run(fmm, A, B, depth=0, precision="fp32")
+    Ah, Al = O.split_tf32(A, "rne")
+    Bh, Bl = O.split_tf32(B, "rne")
+    model = O.split_product(Ah, Al, Bh, Bl)
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
+    assert np.max(np.abs(C - model) / scale) <= 4 * k * 2.0 ** -24
+
+
+def test_tf32_input_conversion_rule(fmm):
+    # Probe of how the tensor core reads fp32 operands in kind::tf32: a = 1 + 0.75 ulp(tf32)
+    # rounds to 1 + 2^-10 to nearest and to 1 under truncation.  The test records which.
+    k = 32
+    A = np.zeros((128, k), np.float32)
+    A[:, 0] = np.float32(1 + 2 ** -11 + 2 ** -12)
+    A[:, 1] = np.float32(1 + 2 ** -12)            # 0.25 ulp: 1 under both rules
+    B = np.zeros((k, 128), np.float32)
+    B[0, :] = 1.0
+    B[1, 1:] = 1.0
+    C, _ = run(fmm, A, B, depth=0, precision="tf32")
+    got0 = float(C[0, 0])
+    assert got0 in (1.0, 1.0 + 2 ** -10), got0
+    print("tf32 conversion:", "truncate" if got0 == 1.0 else "round-to-nearest")
+    assert float(C[0, 1]) == got0 + 1.0
+
+
+def test_blas_semantics(fmm):
+    m, k, n = 130, 70, 90
+    A = I.small_int((m, k), 5, r=3)
+    B = I.small_int((k, n), 6, r=3)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
+    Cnan = np.full((m, n), np.nan, np.float32)
+    for d in (0, 1):
+        C, _ = run(fmm, A, B, Cnan, alpha=2.0, beta=0.0, depth=d)
+        assert np.array_equal(C, (2.0 * ref).astype(np.float32))
+        C0 = I.small_int((m, n), 7, r=5)
+        C, _ = run(fmm, A, B, C0, alpha=1.0, beta=-3.0, depth=d)
+        assert np.array_equal(C, (ref - 3.0 * C0).astype(np.float32))
+        Anan = np.full((m, k), np.nan, np.float32)
+        C, _ = run(fmm, Anan, B, C0, alpha=0.0, beta=0.5, depth=d)
+        assert np.array_equal(C, 0.5 * C0)
+
+
+def test_degenerate_sizes(fmm):
+    import torch
+    C0 = I.small_int((5, 7), 8)
+    C, _ = run(fmm, np.zeros((5, 0), np.float32), np.zeros((0, 7), np.float32), C0, beta=2.0)
+    assert np.array_equal(C, 2.0 * C0)
+    p = fmm.Plan(0, 7, 3)
+    p(torch.empty((0, 3), device="cuda"), torch.empty((3, 7), device="cuda"), torch.empty((0, 7), device="cuda"))
+    p.close()
+
+
+def test_strided_operands(fmm):
+    import torch
+    m, k, n = 192, 160, 200
+    lda, ldb, ldc = 171, 203, 211   # not multiples of 4: unaligned rows
+    A = I.small_int((m, lda), 9)
+    B = I.small_int((k, ldb), 10)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    dC = torch.zeros((m, ldc), device="cuda")
+    ref = O.classical(A[:, :k].astype(np.int64), B[:, :n].astype(np.int64)).astype(np.float32)
+    for d in (0, 1, 2):
+        p = fmm.Plan(m, n, k, lda, ldb, ldc, depth=d)
+        p(dA, dB, dC)
+        torch.cuda.synchronize()
+        got = dC.cpu().numpy()
+        assert np.array_equal(got[:, :n], ref)
+        assert np.all(got[:, n:] == 0)
+        p.close()
