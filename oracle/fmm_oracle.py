@@ -287,11 +287,15 @@ def round_mantissa(x: np.ndarray, keep_bits: int, mode: str = "rne") -> np.ndarr
     return (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
 
 
-def split_tf32(x: np.ndarray, mode: str = "rne"):
-    """x = hi + lo (+ residual): hi = tf32(x), lo = tf32(x - hi); both exact in fp32."""
+def split_tf32(x: np.ndarray, mode: str = "rne", lo_mode: str | None = None):
+    """x = hi + lo (+ residual): hi = tf32(x) rounded by `mode`, lo = tf32(x - hi)
+    rounded by `lo_mode` (default: `mode`); x - hi is exact in fp32.
+
+    ("trunc", "rne") is the split whose hi is what a tensor core that truncates
+    fp32 operands to TF32 reads from the raw value."""
     x = np.asarray(x, dtype=np.float32)
     hi = round_mantissa(x, 10, mode)
-    lo = round_mantissa((x - hi).astype(np.float32), 10, mode)
+    lo = round_mantissa((x - hi).astype(np.float32), 10, lo_mode or mode)
     return hi, lo
 
 

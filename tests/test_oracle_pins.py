@@ -297,12 +297,13 @@ def test_bf16_split_matches_torch_conversion():
 
 def test_tf32_split_reconstructs():
     x = np.concatenate([I.normal((2000,), 9), I.log_uniform((2000,), 10)])
-    for mode in ("rne", "trunc"):
-        hi, lo = O.split_tf32(x, mode)
+    bounds = {("rne", "rne"): 2.0 ** -21, ("trunc", "trunc"): 2.0 ** -20, ("trunc", "rne"): 2.0 ** -21}
+    for (mode, lo_mode), bound in bounds.items():
+        hi, lo = O.split_tf32(x, mode, lo_mode)
         assert np.array_equal(O.round_mantissa(hi, 10, "trunc"), hi)
         assert np.array_equal(O.round_mantissa(lo, 10, "trunc"), lo)
         err = np.abs(hi.astype(np.float64) + lo - x) / np.abs(x)
-        assert err.max() <= (2.0 ** -21 if mode == "rne" else 2.0 ** -20)
+        assert err.max() <= bound, (mode, lo_mode)
 
 
 def test_split_product_error_bound():
