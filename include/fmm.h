@@ -154,6 +154,17 @@ fmm_status_t fmm_get_device_status(fmm_plan_t plan);
 fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* precision,
                            int* odd, int* algo);
 
+/* Phase profiling.  fmm_plan_profile(plan, 1) resets the counters and makes
+ * every later fmm_gemm on the plan record CUDA events (on the call's stream)
+ * around three phases: pre-additions (plus operand copies), the leaf launch,
+ * and post-additions.  fmm_plan_profile_read synchronises on the recorded
+ * events and returns the summed milliseconds per phase, the number of kernel
+ * launches the library made and the number of calls since the reset (any
+ * pointer may be NULL).  Profiling adds no device work beyond event records. */
+fmm_status_t fmm_plan_profile(fmm_plan_t plan, int enable);
+fmm_status_t fmm_plan_profile_read(fmm_plan_t plan, double* pre_ms, double* leaf_ms, double* post_ms,
+                                   int64_t* launches, int64_t* calls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -144,6 +144,13 @@ struct fmm_plan_s {
     long long ld_bt = 0, ld_acopy = 0;
     int num_sms = 0;
     cudaStream_t last_stream = nullptr;
+    // phase profiling: events around pre-additions / leaves / post-additions
+    struct EvSet { cudaEvent_t e[4]; };
+    int profile = 0;
+    EvSet* cur = nullptr;
+    std::vector<EvSet> ev_pending, ev_free;
+    double prof_ms[3] = {0.0, 0.0, 0.0};
+    long long launches = 0, calls = 0;
 };
 
 namespace {
@@ -202,6 +209,24 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
     if (needed) *needed = align_up(cv.off, 256);
 }
 
+inline void mark(fmm_plan_s* p, int i, cudaStream_t s) {
+    if (p->cur) cudaEventRecord(p->cur->e[i], s);
+}
+
+fmm_status_t drain_profile(fmm_plan_s* p) {
+    for (auto& es : p->ev_pending) {
+        FMM_CUDA(cudaEventSynchronize(es.e[3]));
+        for (int i = 0; i < 3; ++i) {
+            float ms = 0.f;
+            FMM_CUDA(cudaEventElapsedTime(&ms, es.e[i], es.e[i + 1]));
+            p->prof_ms[i] += ms;
+        }
+        p->ev_free.push_back(es);
+    }
+    p->ev_pending.clear();
+    return FMM_OK;
+}
+
 fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->depth < -1 || o->depth > 6) return FMM_ERR_INVALID_ARG;
     if (o->leaf_tile != 0 && o->leaf_tile != 128 && o->leaf_tile != 256) return FMM_ERR_INVALID_ARG;
@@ -241,19 +266,23 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream) {
     args.ext_groups = nullptr;
     args.status = p->status;
     FMM_CUDA(launch_leaf_gemm(args, p->mode, p->bn, p->num_sms, stream));
+    p->launches += args.total_tiles > 0 ? 1 : 0;
     return FMM_OK;
 }
 
 fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                            cudaStream_t stream) {
     FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
+    p->launches += 1;
     const float* Aop = A;
     long long lda = p->lda;
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
         FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
+        p->launches += 1;
         Aop = p->Acopy;
         lda = p->ld_acopy;
     }
+    mark(p, 1, stream);
     GemmArgs args;
     memset(&args, 0, sizeof(args));
     fmm_status_t s;
@@ -266,7 +295,9 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
     G.map_a = 0; G.map_b = 1;
     G.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && p->ldc % 4 == 0) ? 1 : 0;
     args.num_groups = 1;
-    return run_leaves(p, args, stream);
+    fmm_status_t st = run_leaves(p, args, stream);
+    mark(p, 2, stream);
+    return st;
 }
 
 fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
@@ -281,6 +312,7 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
         FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
         Stack sb{lv[0].bchild, C1.k, C1.n * C1.k, 7};
         FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->K, p->N, C1.k, C1.n, sb, 1, stream));
+        p->launches += 2;
     }
     // ---- levels 1..d-1
     for (int l = 1; l < d; ++l) {
@@ -294,7 +326,9 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
         Stack sb{L.bchild, Ch.k, Ch.n * Ch.k, per};
         FMM_CUDA(launch_pre_add(va, L.nodes, sa, 0, L.full, stream));
         FMM_CUDA(launch_pre_add(vb, L.nodes, sb, 1, L.full, stream));
+        p->launches += 2;
     }
+    mark(p, 1, stream);
     // ---- leaves
     {
         const Level& Lf = lv[d];      // leaf sizes
@@ -350,6 +384,7 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
         }
         if ((s = run_leaves(p, args, stream)) != FMM_OK) return s;
     }
+    mark(p, 2, stream);
     // ---- post-additions, bottom-up
     for (int l = d - 1; l >= 0; --l) {
         const Level& L = lv[l];
@@ -362,6 +397,7 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
             FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, 1, Ch.m, Ch.n, C, p->ldc, 0, p->M, p->N, alpha, beta,
                                      stream));
         }
+        p->launches += 1;
     }
     return FMM_OK;
 }
@@ -454,8 +490,48 @@ fmm_status_t fmm_gemm(fmm_plan_t p, float alpha, const float* A, const float* B,
         return FMM_OK;
     }
     if (!A || !B) return FMM_ERR_INVALID_ARG;
-    if (p->depth == 0) return run_classical(p, alpha, A, B, beta, C, stream);
-    return run_winograd(p, alpha, A, B, beta, C, stream);
+    fmm_plan_s::EvSet es;
+    if (p->profile) {
+        if (!p->ev_free.empty()) {
+            es = p->ev_free.back();
+            p->ev_free.pop_back();
+        } else {
+            for (int i = 0; i < 4; ++i) FMM_CUDA(cudaEventCreate(&es.e[i]));
+        }
+        p->cur = &es;
+        mark(p, 0, stream);
+    }
+    fmm_status_t st = (p->depth == 0) ? run_classical(p, alpha, A, B, beta, C, stream)
+                                      : run_winograd(p, alpha, A, B, beta, C, stream);
+    p->calls += 1;
+    if (p->cur) {
+        mark(p, 3, stream);
+        p->cur = nullptr;
+        p->ev_pending.push_back(es);
+    }
+    return st;
+}
+
+fmm_status_t fmm_plan_profile(fmm_plan_t p, int enable) {
+    if (!p) return FMM_ERR_INVALID_ARG;
+    fmm_status_t s = drain_profile(p);
+    p->profile = enable ? 1 : 0;
+    p->prof_ms[0] = p->prof_ms[1] = p->prof_ms[2] = 0.0;
+    p->launches = 0;
+    p->calls = 0;
+    return s;
+}
+
+fmm_status_t fmm_plan_profile_read(fmm_plan_t p, double* pre_ms, double* leaf_ms, double* post_ms,
+                                   int64_t* launches, int64_t* calls) {
+    if (!p) return FMM_ERR_INVALID_ARG;
+    fmm_status_t s = drain_profile(p);
+    if (pre_ms) *pre_ms = p->prof_ms[0];
+    if (leaf_ms) *leaf_ms = p->prof_ms[1];
+    if (post_ms) *post_ms = p->prof_ms[2];
+    if (launches) *launches = p->launches;
+    if (calls) *calls = p->calls;
+    return s;
 }
 
 fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, const int64_t* K, const float* const* A,
@@ -467,7 +543,13 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
     return FMM_ERR_UNSUPPORTED;
 }
 
-void fmm_free(fmm_plan_t p) { delete p; }
+void fmm_free(fmm_plan_t p) {
+    if (!p) return;
+    drain_profile(p);
+    for (auto& es : p->ev_free)
+        for (int i = 0; i < 4; ++i) cudaEventDestroy(es.e[i]);
+    delete p;
+}
 
 fmm_status_t fmm_get_device_status(fmm_plan_t p) {
     if (!p) return FMM_ERR_INVALID_ARG;

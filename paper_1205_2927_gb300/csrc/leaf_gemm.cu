@@ -13,9 +13,11 @@
 //                 into a double-buffered TMEM accumulator (2 x BN columns)
 //   warp 2        TMEM allocation / release
 //   warps 4..7    epilogue: tcgen05.ld -> alpha/beta -> global stores
-//   warps 8..11   (3xTF32 only) split each landed stage in place into
-//                 hi = tf32(x) and a lo = tf32(x - hi) copy, so that the MMA
-//                 warp issues lo*hi + hi*lo + hi*hi with fp32 accumulation.
+//   warps 8..11   (3xTF32 only) write lo = tf32_rn(x - trunc_tf32(x)) of each
+//                 landed stage into a second buffer; the tensor core reads
+//                 the raw fp32 tile as hi (kind::tf32 truncates its operands
+//                 to 10 mantissa bits on sm_103a, which the GPU tests pin), so
+//                 the MMA warp issues lo*hi + hi*lo + hi*hi, fp32 accumulate.
 // Every mbarrier wait is bounded (ptx.cuh): a broken pipeline records a
 // timeout in the status word and the kernel returns.
 #include "fmm_internal.h"
@@ -253,12 +255,11 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
 #pragma unroll 4
                 for (int i = tid; i < Cfg::kStageBytes / 16; i += 128) {
                     const float4 v = src[i];
-                    float4 h, l;
-                    h.x = tf32_round_rne(v.x); l.x = tf32_round_rne(v.x - h.x);
-                    h.y = tf32_round_rne(v.y); l.y = tf32_round_rne(v.y - h.y);
-                    h.z = tf32_round_rne(v.z); l.z = tf32_round_rne(v.z - h.z);
-                    h.w = tf32_round_rne(v.w); l.w = tf32_round_rne(v.w - h.w);
-                    src[i] = h;
+                    float4 l;
+                    l.x = tf32_round_rne(v.x - tf32_trunc(v.x));
+                    l.y = tf32_round_rne(v.y - tf32_trunc(v.y));
+                    l.z = tf32_round_rne(v.z - tf32_trunc(v.z));
+                    l.w = tf32_round_rne(v.w - tf32_trunc(v.w));
                     dst[i] = l;
                 }
                 fence_proxy_async_smem();

@@ -167,6 +167,9 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The TF32 value the tensor core reads from an fp32 operand (low 13 bits cleared).
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 // Round an fp32 value to the nearest TF32 value (10 explicit mantissa bits),
 // ties to even, by integer arithmetic on the bit pattern.  Finite inputs.
 __device__ __forceinline__ float tf32_round_rne(float x) {

@@ -71,6 +71,11 @@ def _load():
     lib.fmm_get_device_status.restype = C.c_int
     lib.fmm_plan_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 5
     lib.fmm_plan_info.restype = C.c_int
+    lib.fmm_plan_profile.argtypes = [vp, C.c_int]
+    lib.fmm_plan_profile.restype = C.c_int
+    lib.fmm_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i64)]
+    lib.fmm_plan_profile_read.restype = C.c_int
     return lib
 
 
@@ -141,6 +146,16 @@ def fmm_plan_info(plan):
     return dict(zip(("depth", "leaf_tile", "precision", "odd", "algo"), [v.value for v in vals]))
 
 
+def fmm_plan_profile(plan, enable=True):
+    _check(_lib.fmm_plan_profile(plan, int(bool(enable))), "fmm_plan_profile")
+
+
+def fmm_plan_profile_read(plan):
+    v = [C.c_double() for _ in range(3)] + [C.c_int64(), C.c_int64()]
+    _check(_lib.fmm_plan_profile_read(plan, *[C.byref(x) for x in v]), "fmm_plan_profile_read")
+    return dict(pre_ms=v[0].value, leaf_ms=v[1].value, post_ms=v[2].value, launches=v[3].value, calls=v[4].value)
+
+
 # ------------------------------------------------------------------ convenience over torch tensors
 
 class Plan:
@@ -172,6 +187,12 @@ class Plan:
 
     def device_status(self):
         return fmm_get_device_status(self.handle)
+
+    def profile(self, enable=True):
+        fmm_plan_profile(self.handle, enable)
+
+    def profile_read(self):
+        return fmm_plan_profile_read(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -84,13 +84,15 @@ def test_tf32_is_coarser_than_fp32(fmm):
 
 
 def test_fp32_matches_three_product_split_model(fmm):
-    # the 3xTF32 leaf equals hi*hi + hi*lo + lo*hi (round-to-nearest splits)
-    # up to fp32 accumulation error, far tighter than the error bound
+    # the 3xTF32 leaf equals hi*hi + hi*lo + lo*hi with hi = trunc_tf32(x) (what the
+    # tensor core reads from the raw operand) and lo = rn_tf32(x - hi), up to fp32
+    # accumulation error -- far tighter than the error bound; a dropped or
+    # mis-split term is off by ~2^-11 relative
     m, k, n = 256, 512, 256
     A, B = I.operands(m, k, n, 77)
     C, _ = run(fmm, A, B, depth=0, precision="fp32")
-    Ah, Al = O.split_tf32(A, "rne")
-    Bh, Bl = O.split_tf32(B, "rne")
+    Ah, Al = O.split_tf32(A, "trunc", "rne")
+    Bh, Bl = O.split_tf32(B, "trunc", "rne")
     model = O.split_product(Ah, Al, Bh, Bl)
     scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
     assert np.max(np.abs(C - model) / scale) <= 4 * k * 2.0 ** -24
