@@ -135,6 +135,28 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
                               const fmm_options_t* opt, void* workspace, size_t workspace_bytes,
                               size_t* workspace_needed, fmm_stream_t stream);
 
+/* Batched plan: the same products as fmm_gemm_batched, split so that the
+ * launches can be captured in a CUDA graph and replayed.  fmm_batched_plan
+ * picks each problem's depth (opt->depth, or the fixed planner per problem),
+ * encodes every tensor map and leaf descriptor and copies the tables into the
+ * workspace (synchronously); fmm_batched_run then only launches kernels: one
+ * batched transpose/copy launch, the pre-additions of the problems that
+ * recurse, ONE persistent leaf launch over every leaf product of every problem
+ * (longest tiles first), and the post-additions.  The operand pointers are
+ * bound at plan time.  With out == NULL only *workspace_needed is set. */
+typedef struct fmm_batched_s* fmm_batched_t;
+fmm_status_t fmm_batched_plan(fmm_batched_t* out, int count, const int64_t* M, const int64_t* N,
+                              const int64_t* K, const float* const* A, const int64_t* lda,
+                              const float* const* B, const int64_t* ldb, float* const* C,
+                              const int64_t* ldc, const float* alpha, const float* beta,
+                              const fmm_options_t* opt, void* workspace, size_t workspace_bytes,
+                              size_t* workspace_needed, fmm_stream_t stream);
+fmm_status_t fmm_batched_run(fmm_batched_t plan, fmm_stream_t stream);
+void fmm_batched_free(fmm_batched_t plan);
+/* depths: `count` ints (-1 for problems with no product to compute); any
+ * pointer may be NULL.  launches: kernels launched by all runs so far. */
+fmm_status_t fmm_batched_info(fmm_batched_t plan, int* depths, int64_t* total_tiles, int64_t* launches);
+
 /* Release a plan (NULL-safe).  Never frees the caller's workspace. */
 void fmm_free(fmm_plan_t plan);
 
@@ -153,6 +175,18 @@ fmm_status_t fmm_get_device_status(fmm_plan_t plan);
  * uses (after the planner ran); any pointer may be NULL. */
 fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* precision,
                            int* odd, int* algo);
+
+/* Freivalds residual of a computed product: r = C x - A (B x) for a probe
+ * vector x (N entries, device; +-1 entries make a single wrong C entry show up
+ * exactly in r).  A (M x K), B (K x N), C (M x N) row-major device matrices;
+ * r: M doubles (device).  fp64 = 0 accumulates in fp32, fp64 = 1 in float64
+ * (the optional one-step fp64 refinement of the residual).  workspace: device
+ * memory of *workspace_needed bytes (K + M doubles); with workspace and r both
+ * NULL only *workspace_needed is set.  Asynchronous; one pass over A, B, C. */
+fmm_status_t fmm_residual(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                          const float* B, int64_t ldb, const float* C, int64_t ldc,
+                          const float* x, double* r, void* workspace, size_t workspace_bytes,
+                          size_t* workspace_needed, int fp64, fmm_stream_t stream);
 
 /* Phase profiling.  fmm_plan_profile(plan, 1) resets the counters and makes
  * every later fmm_gemm on the plan record CUDA events (on the call's stream)

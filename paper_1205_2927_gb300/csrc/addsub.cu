@@ -245,6 +245,39 @@ __global__ void scale_kernel(float* C, long long ldc, long long M, long long N, 
         if (c < N) C[r * ldc + c] = (beta == 0.0f) ? 0.0f : beta * C[r * ldc + c];
 }
 
+__global__ void __launch_bounds__(256) batched_copy_kernel(const CopyJob* __restrict__ jobs, int njobs) {
+    __shared__ float tile[32][33];
+    const long long t = blockIdx.x;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    const CopyJob J = jobs[lo];
+    const long long local = t - J.tile_begin;
+    const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (!J.transpose) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long r = r0 + ty + 8 * i, c = c0 + tx;
+            if (r < J.rows && c < J.cols) J.dst[r * J.ldd + c] = J.src[r * J.lds + c];
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long r = r0 + ty + 8 * i, c = c0 + tx;
+        tile[ty + 8 * i][tx] = (r < J.rows && c < J.cols) ? J.src[r * J.lds + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long c = c0 + ty + 8 * i, r = r0 + tx;
+        if (c < J.cols && r < J.rows) J.dst[c * J.ldd + r] = tile[tx][ty + 8 * i];
+    }
+}
+
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -310,6 +343,12 @@ cudaError_t launch_copy2d(const float* A, long long lda, long long M, long long 
     if (M <= 0 || K <= 0) return cudaSuccess;
     dim3 grid((unsigned)((K + 255) / 256), gy(M));
     copy2d_kernel<<<grid, 256, 0, stream>>>(A, lda, M, K, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, long long total_tiles, cudaStream_t stream) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    batched_copy_kernel<<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -134,6 +135,9 @@ struct fmm_plan_s {
     int bn;
     int mode;                 // LeafMode
     long long M0, K0, N0;     // padded root sizes (Winograd)
+    long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
+    int peel = 0;
+    float border_beta = 0.f;
     char* ws = nullptr;
     size_t ws_bytes = 0;
     unsigned* status = nullptr;
@@ -182,9 +186,21 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         p->Acopy = cv.take<float>((size_t)p->M * p->ld_acopy);
     } else {
         const long long g = 4LL << d;
-        p->M0 = rup(p->M, g);
-        p->K0 = rup(p->K, g);
-        p->N0 = rup(p->N, g);
+        if (p->peel) {
+            p->Mw = p->M / g * g;
+            p->Kw = p->K / g * g;
+            p->Nw = p->N / g * g;
+            p->M0 = p->Mw;
+            p->K0 = p->Kw;
+            p->N0 = p->Nw;
+        } else {
+            p->Mw = p->M;
+            p->Kw = p->K;
+            p->Nw = p->N;
+            p->M0 = rup(p->M, g);
+            p->K0 = rup(p->K, g);
+            p->N0 = rup(p->N, g);
+        }
         for (int l = 0; l <= d; ++l) {
             p->lv[l].m = p->M0 >> l;
             p->lv[l].k = p->K0 >> l;
@@ -204,6 +220,13 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         for (int l = 1; l < d; ++l) {
             Level& L = p->lv[l];
             L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
+        }
+        if (p->peel && (p->Mw < p->M || p->Kw < p->K || p->Nw < p->N)) {
+            // border products (classical leaves) read B transposed and A TMA-aligned
+            p->ld_bt = rup(p->K, 4);
+            p->Bt = cv.take<float>((size_t)p->N * p->ld_bt);
+            p->ld_acopy = rup(p->K, 4);
+            p->Acopy = cv.take<float>((size_t)p->M * p->ld_acopy);
         }
     }
     if (needed) *needed = align_up(cv.off, 256);
@@ -235,7 +258,7 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
     if (o->precision == FMM_PREC_BF16X3 || o->precision == FMM_PREC_FP16X3) return FMM_ERR_UNSUPPORTED;
-    if (o->odd == FMM_ODD_PEEL || o->algo == FMM_ALGO_CLASSICAL || o->host_operands) return FMM_ERR_UNSUPPORTED;
+    if (o->algo == FMM_ALGO_CLASSICAL || o->host_operands) return FMM_ERR_UNSUPPORTED;
     return FMM_OK;
 }
 
@@ -300,21 +323,66 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
     return st;
 }
 
-fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
-                          cudaStream_t stream) {
+// Peeled border of a Winograd call on the even core (Mw x Kw x Nw), as classical
+// tensor-core leaves in one launch (dynamic peeling, generalised from one row /
+// column to the remainder modulo the level granule):
+//   K > Kw:  C[:Mw, :Nw] += alpha * A[:Mw, Kw:] B[Kw:, :Nw]   (after the core)
+//   M > Mw:  C[Mw:, :]    = alpha * A[Mw:, :] B + beta * C[Mw:, :]
+//   N > Nw:  C[:Mw, Nw:]  = alpha * A[:Mw, :] B[:, Nw:] + beta * C[:Mw, Nw:]
+fmm_status_t run_border(fmm_plan_s* p, float alpha, const float* A, const float* B, float* C, cudaStream_t stream) {
+    FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
+    p->launches += 1;
+    const float* Aop = A;
+    long long lda = p->lda;
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
+        FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
+        p->launches += 1;
+        Aop = p->Acopy;
+        lda = p->ld_acopy;
+    }
+    const long long ldt = p->ld_bt;
+    const bool cvec = (reinterpret_cast<uintptr_t>(C) & 15) == 0 && p->ldc % 4 == 0;
+    GemmArgs args;
+    memset(&args, 0, sizeof(args));
+    int ng = 0, nm = 0;
+    fmm_status_t s;
+    auto add = [&](const float* a, long long a_cols, long long a_rows, const float* b, long long b_rows, float* c,
+                   long long M, long long N, long long K, float al, float be) -> fmm_status_t {
+        if (M <= 0 || N <= 0 || K <= 0) return FMM_OK;
+        fmm_status_t st;
+        if ((st = encode_map(&args.maps[nm], a, a_cols, a_rows, 1, lda, a_rows * lda, kBM)) != FMM_OK) return st;
+        if ((st = encode_map(&args.maps[nm + 1], b, a_cols, b_rows, 1, ldt, b_rows * ldt, p->bn)) != FMM_OK) return st;
+        GemmGroup& G = args.groups[ng++];
+        G.M = (int)M; G.N = (int)N; G.K = (int)K; G.batch = 1;
+        G.C = c; G.ldc = p->ldc; G.c_batch_stride = 0; G.alpha = al; G.beta = be;
+        G.map_a = nm; G.map_b = nm + 1; G.vec_ok = cvec ? 1 : 0;
+        nm += 2;
+        return FMM_OK;
+    };
+    const long long Mw = p->Mw, Kw = p->Kw, Nw = p->Nw, M = p->M, N = p->N, K = p->K;
+    if ((s = add(Aop + Kw, K - Kw, Mw, p->Bt + Kw, Nw, C, Mw, Nw, K - Kw, alpha, 1.0f)) != FMM_OK) return s;
+    if ((s = add(Aop + Mw * lda, K, M - Mw, p->Bt, N, C + Mw * p->ldc, M - Mw, N, K, alpha, p->border_beta)) != FMM_OK)
+        return s;
+    if ((s = add(Aop, K, Mw, p->Bt + Nw * ldt, N - Nw, C + Nw, Mw, N - Nw, K, alpha, p->border_beta)) != FMM_OK)
+        return s;
+    args.num_groups = ng;
+    if (ng == 0) return FMM_OK;
+    return run_leaves(p, args, stream);
+}
+
+// Pre-additions of every level (breadth-first), reading the caller's A and B at the root.
+fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStream_t stream) {
     const int d = p->depth;
     Level* lv = p->lv;
-    // ---- level 0: root pre-additions (always all 7 children)
     {
         const Level& C1 = lv[1];
-        View va{A, p->lda, 0, lv[0].m, lv[0].k, p->M, p->K};
+        View va{A, p->lda, 0, lv[0].m, lv[0].k, p->Mw, p->Kw};
         Stack sa{lv[0].achild, C1.k, C1.m * C1.k, 7};
         FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
         Stack sb{lv[0].bchild, C1.k, C1.n * C1.k, 7};
-        FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->K, p->N, C1.k, C1.n, sb, 1, stream));
+        FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, 1, stream));
         p->launches += 2;
     }
-    // ---- levels 1..d-1
     for (int l = 1; l < d; ++l) {
         const Level& L = lv[l];
         const Level& Ch = lv[l + 1];
@@ -328,64 +396,72 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
         FMM_CUDA(launch_pre_add(vb, L.nodes, sb, 1, L.full, stream));
         p->launches += 2;
     }
-    mark(p, 1, stream);
-    // ---- leaves
-    {
-        const Level& Lf = lv[d];      // leaf sizes
-        const Level& Ll = lv[d - 1];  // last recursion level
-        GemmArgs args;
-        memset(&args, 0, sizeof(args));
-        fmm_status_t s;
-        const long long mm = Lf.m, kk = Lf.k, nn = Lf.n;
-        if (Ll.full) {
-            const long long batch = Lf.nodes;
-            if ((s = encode_map(&args.maps[0], Ll.achild, kk, mm, batch, kk, mm * kk, kBM)) != FMM_OK) return s;
-            if ((s = encode_map(&args.maps[1], Ll.bchild, kk, nn, batch, kk, nn * kk, p->bn)) != FMM_OK) return s;
-            GemmGroup& G = args.groups[0];
-            G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)batch;
-            G.C = p->P; G.ldc = nn; G.c_batch_stride = mm * nn;
-            G.alpha = 1.f; G.beta = 0.f; G.map_a = 0; G.map_b = 1; G.vec_ok = 1;
-            args.num_groups = 1;
-        } else {
-            // parent operands of the last level: stacks of Ll.nodes matrices (Ll.m x Ll.k, Ll.n x Ll.k)
-            const Level& Pa = lv[d - 2];
-            const float* pa = Pa.achild;
-            const float* pb = Pa.bchild;
-            const long long nodes = Ll.nodes;
-            const long long ka = Ll.k;  // parent row length
-            // A-side operand maps: 0..2 quadrant views Q0, Q1, Q3; 3..6 sums S1..S4
-            auto qa = [&](int qi, int qj) { return pa + qi * mm * ka + qj * kk; };
-            auto qb = [&](int qi, int qj) { return pb + qi * nn * ka + qj * kk; };
-            if ((s = encode_map(&args.maps[0], qa(0, 0), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
-            if ((s = encode_map(&args.maps[1], qa(0, 1), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
-            if ((s = encode_map(&args.maps[2], qa(1, 1), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
-            for (int j = 0; j < 4; ++j)
-                if ((s = encode_map(&args.maps[3 + j], Ll.achild + j * mm * kk, kk, mm, nodes, kk, 4 * mm * kk, kBM)) !=
-                    FMM_OK)
-                    return s;
-            // B side (transposed): 7..9 views Y0, Y1, Y3; 10..13 sums T1..T4
-            if ((s = encode_map(&args.maps[7], qb(0, 0), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
-            if ((s = encode_map(&args.maps[8], qb(0, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
-            if ((s = encode_map(&args.maps[9], qb(1, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
-            for (int j = 0; j < 4; ++j)
-                if ((s = encode_map(&args.maps[10 + j], Ll.bchild + j * nn * kk, kk, nn, nodes, kk, 4 * nn * kk,
-                                    p->bn)) != FMM_OK)
-                    return s;
-            //                P1  P2  P3  P4  P5  P6  P7
-            const int amap[7] = {0, 1, 6, 2, 3, 4, 5};     // Q0, Q1, S4, Q3, S1, S2, S3
-            const int bmap[7] = {7, 8, 9, 13, 10, 11, 12}; // Y0, Y1, Y3, T4, T1, T2, T3
-            for (int i = 0; i < 7; ++i) {
-                GemmGroup& G = args.groups[i];
-                G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)nodes;
-                G.C = p->P + i * mm * nn; G.ldc = nn; G.c_batch_stride = 7 * mm * nn;
-                G.alpha = 1.f; G.beta = 0.f; G.map_a = amap[i]; G.map_b = bmap[i]; G.vec_ok = 1;
-            }
-            args.num_groups = 7;
-        }
-        if ((s = run_leaves(p, args, stream)) != FMM_OK) return s;
+    return FMM_OK;
+}
+
+// Append the leaf groups of the plan's last level (and their tensor maps) to
+// the given arrays; map indices are absolute in `maps`.
+fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, GemmGroup* groups, int& ng) {
+    const int d = p->depth;
+    Level* lv = p->lv;
+    const Level& Lf = lv[d];      // leaf sizes
+    const Level& Ll = lv[d - 1];  // last recursion level
+    fmm_status_t s;
+    const long long mm = Lf.m, kk = Lf.k, nn = Lf.n;
+    if (Ll.full) {
+        const long long batch = Lf.nodes;
+        if ((s = encode_map(&maps[nm], Ll.achild, kk, mm, batch, kk, mm * kk, kBM)) != FMM_OK) return s;
+        if ((s = encode_map(&maps[nm + 1], Ll.bchild, kk, nn, batch, kk, nn * kk, p->bn)) != FMM_OK) return s;
+        GemmGroup& G = groups[ng++];
+        memset(&G, 0, sizeof(G));
+        G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)batch;
+        G.C = p->P; G.ldc = nn; G.c_batch_stride = mm * nn;
+        G.alpha = 1.f; G.beta = 0.f; G.map_a = nm; G.map_b = nm + 1; G.vec_ok = 1;
+        nm += 2;
+        return FMM_OK;
     }
-    mark(p, 2, stream);
-    // ---- post-additions, bottom-up
+    // parent operands of the last level: stacks of Ll.nodes matrices (Ll.m x Ll.k, Ll.n x Ll.k)
+    const Level& Pa = lv[d - 2];
+    const float* pa = Pa.achild;
+    const float* pb = Pa.bchild;
+    const long long nodes = Ll.nodes;
+    const long long ka = Ll.k;  // parent row length
+    auto qa = [&](int qi, int qj) { return pa + qi * mm * ka + qj * kk; };
+    auto qb = [&](int qi, int qj) { return pb + qi * nn * ka + qj * kk; };
+    const int b0 = nm;
+    // A side: b0+0..2 quadrant views Q0, Q1, Q3; b0+3..6 sums S1..S4
+    if ((s = encode_map(&maps[b0 + 0], qa(0, 0), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
+    if ((s = encode_map(&maps[b0 + 1], qa(0, 1), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
+    if ((s = encode_map(&maps[b0 + 2], qa(1, 1), kk, mm, nodes, ka, Ll.m * ka, kBM)) != FMM_OK) return s;
+    for (int j = 0; j < 4; ++j)
+        if ((s = encode_map(&maps[b0 + 3 + j], Ll.achild + j * mm * kk, kk, mm, nodes, kk, 4 * mm * kk, kBM)) != FMM_OK)
+            return s;
+    // B side (transposed): b0+7..9 views Y0, Y1, Y3; b0+10..13 sums T1..T4
+    if ((s = encode_map(&maps[b0 + 7], qb(0, 0), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+    if ((s = encode_map(&maps[b0 + 8], qb(0, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+    if ((s = encode_map(&maps[b0 + 9], qb(1, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+    for (int j = 0; j < 4; ++j)
+        if ((s = encode_map(&maps[b0 + 10 + j], Ll.bchild + j * nn * kk, kk, nn, nodes, kk, 4 * nn * kk, p->bn)) !=
+            FMM_OK)
+            return s;
+    //                       P1  P2  P3  P4  P5  P6  P7
+    const int amap[7] = {0, 1, 6, 2, 3, 4, 5};       // Q0, Q1, S4, Q3, S1, S2, S3
+    const int bmap[7] = {7, 8, 9, 13, 10, 11, 12};   // Y0, Y1, Y3, T4, T1, T2, T3
+    for (int i = 0; i < 7; ++i) {
+        GemmGroup& G = groups[ng++];
+        memset(&G, 0, sizeof(G));
+        G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)nodes;
+        G.C = p->P + i * mm * nn; G.ldc = nn; G.c_batch_stride = 7 * mm * nn;
+        G.alpha = 1.f; G.beta = 0.f; G.map_a = b0 + amap[i]; G.map_b = b0 + bmap[i]; G.vec_ok = 1;
+    }
+    nm += 14;
+    return FMM_OK;
+}
+
+// Post-additions bottom-up; the root applies alpha/beta into the caller's C.
+fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cudaStream_t stream) {
+    const int d = p->depth;
+    Level* lv = p->lv;
     for (int l = d - 1; l >= 0; --l) {
         const Level& L = lv[l];
         const Level& Ch = lv[l + 1];
@@ -394,7 +470,7 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
             FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, L.nodes, Ch.m, Ch.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
                                      0.f, stream));
         } else {
-            FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, 1, Ch.m, Ch.n, C, p->ldc, 0, p->M, p->N, alpha, beta,
+            FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, 1, Ch.m, Ch.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
                                      stream));
         }
         p->launches += 1;
@@ -402,9 +478,276 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
     return FMM_OK;
 }
 
+fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
+                          cudaStream_t stream) {
+    p->border_beta = beta;
+    fmm_status_t s;
+    if ((s = winograd_pre(p, A, B, stream)) != FMM_OK) return s;
+    mark(p, 1, stream);
+    {
+        GemmArgs args;
+        memset(&args, 0, sizeof(args));
+        int nm = 0, ng = 0;
+        if ((s = winograd_leaf_groups(p, args.maps, nm, args.groups, ng)) != FMM_OK) return s;
+        args.num_groups = ng;
+        if ((s = run_leaves(p, args, stream)) != FMM_OK) return s;
+    }
+    mark(p, 2, stream);
+    if ((s = winograd_post(p, alpha, beta, C, stream)) != FMM_OK) return s;
+    if (p->peel && (p->Mw < p->M || p->Kw < p->K || p->Nw < p->N)) return run_border(p, alpha, A, B, C, stream);
+    return FMM_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------------------- batched
+struct fmm_batched_s {
+    int count = 0;
+    int bn = 256, mode = kLeaf3xTF32, num_sms = 0;
+    unsigned* status = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    GemmGroup* d_groups = nullptr;
+    int num_groups = 0;
+    long long total_tiles = 0;
+    CopyJob* d_jobs = nullptr;
+    int njobs = 0;
+    long long job_tiles = 0;
+    std::vector<fmm_plan_s*> subs;     // Winograd sub-plans (problems with depth >= 1)
+    std::vector<int> sub_problem;
+    std::vector<int> depth;            // per problem
+    std::vector<int> scale_only;       // problems with K == 0 or alpha == 0: C <- beta C
+    std::vector<const float*> A, B;
+    std::vector<float*> C;
+    std::vector<long long> M, N, ldc;
+    std::vector<float> alpha, beta;
+    long long launches = 0;
+    ~fmm_batched_s() {
+        for (auto* q : subs) delete q;
+    }
+};
+
+namespace {
+
+fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const int64_t* N, const int64_t* K,
+                           const float* const* A, const int64_t* lda, const float* const* B, const int64_t* ldb,
+                           float* const* C, const int64_t* ldc, const float* alpha, const float* beta,
+                           const fmm_options_t& o, char* ws, size_t* needed) {
+    Carver cv(ws);
+    b->status = cv.take<unsigned>(64);
+    b->count = count;
+    b->bn = o.leaf_tile ? o.leaf_tile : 256;
+    b->mode = (o.precision == FMM_PREC_TF32) ? kLeafTF32 : kLeaf3xTF32;
+    // per-problem depth and resource counts
+    int total_maps = 0, total_groups = 0, total_jobs = 0;
+    b->depth.assign(count, 0);
+    b->scale_only.assign(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (M[i] == 0 || N[i] == 0) { b->depth[i] = -1; continue; }
+        if (K[i] == 0 || alpha[i] == 0.0f) { b->depth[i] = -1; b->scale_only[i] = 1; continue; }
+        int d = o.depth >= 0 ? o.depth : fixed_depth(M[i], N[i], K[i], o.cutoff);
+        const long long mn = std::min(std::min((long long)M[i], (long long)N[i]), (long long)K[i]);
+        while (d > 0 && (mn >> d) < 64) --d;  // keep leaves at least 64 wide
+        b->depth[i] = d;
+        if (d == 0) { total_maps += 2; total_groups += 1; total_jobs += 2; }
+        else { total_maps += 14; total_groups += 7; }
+    }
+    b->d_maps = cv.take<CUtensorMap>(total_maps > 0 ? total_maps : 1);
+    b->d_groups = cv.take<GemmGroup>(total_groups > 0 ? total_groups : 1);
+    b->d_jobs = cv.take<CopyJob>(total_jobs > 0 ? total_jobs : 1);
+    std::vector<CUtensorMap> maps(total_maps > 0 ? total_maps : 1);
+    std::vector<GemmGroup> groups(total_groups > 0 ? total_groups : 1);
+    std::vector<CopyJob> jobs;
+    int nm = 0, ng = 0;
+    for (int i = 0; i < count; ++i) {
+        const int d = b->depth[i];
+        if (d < 0) continue;
+        if (d == 0) {
+            const long long ldt = rup(K[i], 4);
+            float* Bt = cv.take<float>((size_t)N[i] * ldt);
+            const float* Aop = A[i];
+            long long la = lda[i];
+            float* Acopy = nullptr;
+            if (!A || (reinterpret_cast<uintptr_t>(A[i]) & 15) || (lda[i] % 4)) {  // size query: assume a copy
+                la = rup(K[i], 4);
+                Acopy = cv.take<float>((size_t)M[i] * la);
+                Aop = Acopy;
+            }
+            if (!ws) continue;
+            jobs.push_back(CopyJob{B[i], ldb[i], K[i], N[i], Bt, ldt, 0, (int)((N[i] + 31) / 32), 1});
+            if (Acopy) jobs.push_back(CopyJob{A[i], lda[i], M[i], K[i], Acopy, la, 0, (int)((K[i] + 31) / 32), 0});
+            fmm_status_t s;
+            if ((s = encode_map(&maps[nm], Aop, K[i], M[i], 1, la, M[i] * la, kBM)) != FMM_OK) return s;
+            if ((s = encode_map(&maps[nm + 1], Bt, K[i], N[i], 1, ldt, N[i] * ldt, b->bn)) != FMM_OK) return s;
+            GemmGroup& G = groups[ng++];
+            memset(&G, 0, sizeof(G));
+            G.M = (int)M[i]; G.N = (int)N[i]; G.K = (int)K[i]; G.batch = 1;
+            G.C = C[i]; G.ldc = ldc[i]; G.alpha = alpha[i]; G.beta = beta[i];
+            G.map_a = nm; G.map_b = nm + 1;
+            G.vec_ok = ((reinterpret_cast<uintptr_t>(C[i]) & 15) == 0 && ldc[i] % 4 == 0) ? 1 : 0;
+            nm += 2;
+        } else {
+            fmm_plan_s tmp;
+            tmp.M = M[i]; tmp.N = N[i]; tmp.K = K[i]; tmp.lda = lda[i]; tmp.ldb = ldb[i]; tmp.ldc = ldc[i];
+            tmp.opt = o;
+            tmp.depth = d;
+            tmp.bn = b->bn;
+            tmp.mode = b->mode;
+            tmp.peel = 0;
+            size_t need = 0;
+            layout(&tmp, nullptr, &need);
+            char* sub_ws = cv.take<char>(need);
+            if (!ws) continue;
+            fmm_plan_s* q = new (std::nothrow) fmm_plan_s(tmp);
+            if (!q) return FMM_ERR_OOM;
+            layout(q, sub_ws, nullptr);
+            q->status = b->status;
+            b->subs.push_back(q);
+            b->sub_problem.push_back(i);
+            fmm_status_t s;
+            if ((s = winograd_leaf_groups(q, maps.data(), nm, groups.data(), ng)) != FMM_OK) return s;
+        }
+    }
+    if (needed) *needed = align_up(cv.off, 256);
+    if (!ws) return FMM_OK;
+    // longest tiles (largest K) first: round-robin tile assignment then balances like LPT
+    std::stable_sort(groups.begin(), groups.begin() + ng,
+                     [](const GemmGroup& x, const GemmGroup& y) { return x.K > y.K; });
+    long long t = 0;
+    for (int g = 0; g < ng; ++g) {
+        GemmGroup& G = groups[g];
+        G.tiles_m = (G.M + kBM - 1) / kBM;
+        G.tiles_n = (G.N + b->bn - 1) / b->bn;
+        G.tile_begin = t;
+        t += (long long)G.tiles_m * G.tiles_n * G.batch;
+    }
+    b->num_groups = ng;
+    b->total_tiles = t;
+    long long jt = 0;
+    for (auto& J : jobs) {
+        J.tile_begin = jt;
+        jt += ((J.rows + 31) / 32) * (long long)J.tiles_c;
+    }
+    b->njobs = (int)jobs.size();
+    b->job_tiles = jt;
+    FMM_CUDA(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * (nm > 0 ? nm : 1), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemcpy(b->d_groups, groups.data(), sizeof(GemmGroup) * (ng > 0 ? ng : 1), cudaMemcpyHostToDevice));
+    if (!jobs.empty())
+        FMM_CUDA(cudaMemcpy(b->d_jobs, jobs.data(), sizeof(CopyJob) * jobs.size(), cudaMemcpyHostToDevice));
+    FMM_CUDA(cudaMemset(b->status, 0, 64 * sizeof(unsigned)));
+    for (int i = 0; i < count; ++i) {
+        b->A.push_back(A[i]); b->B.push_back(B[i]); b->C.push_back(C[i]);
+        b->M.push_back(M[i]); b->N.push_back(N[i]); b->ldc.push_back(ldc[i]);
+        b->alpha.push_back(alpha[i]); b->beta.push_back(beta[i]);
+    }
+    return FMM_OK;
+}
+
+fmm_status_t batched_check(int count, const int64_t* M, const int64_t* N, const int64_t* K, const float* const* A,
+                           const int64_t* lda, const float* const* B, const int64_t* ldb, float* const* C,
+                           const int64_t* ldc, const float* alpha, const float* beta, const fmm_options_t* opt) {
+    if (count < 0 || (count > 0 && (!M || !N || !K || !lda || !ldb || !ldc || !alpha || !beta))) return FMM_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (M[i] < 0 || N[i] < 0 || K[i] < 0 || M[i] > INT32_MAX || N[i] > INT32_MAX || K[i] > INT32_MAX)
+            return FMM_ERR_INVALID_ARG;
+        if (lda[i] < (K[i] > 0 ? K[i] : 1) || ldb[i] < (N[i] > 0 ? N[i] : 1) || ldc[i] < (N[i] > 0 ? N[i] : 1))
+            return FMM_ERR_INVALID_ARG;
+    }
+    if (opt) {
+        fmm_status_t s = check_opts(opt);
+        if (s != FMM_OK) return s;
+        if (opt->odd != FMM_ODD_PAD) return FMM_ERR_UNSUPPORTED;
+    }
+    (void)A; (void)B; (void)C;
+    return FMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+fmm_status_t fmm_batched_plan(fmm_batched_t* out, int count, const int64_t* M, const int64_t* N, const int64_t* K,
+                              const float* const* A, const int64_t* lda, const float* const* B, const int64_t* ldb,
+                              float* const* C, const int64_t* ldc, const float* alpha, const float* beta,
+                              const fmm_options_t* opt, void* workspace, size_t workspace_bytes,
+                              size_t* workspace_needed, fmm_stream_t stream) {
+    (void)stream;
+    if (out) *out = nullptr;
+    fmm_status_t s = batched_check(count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, opt);
+    if (s != FMM_OK) return s;
+    fmm_options_t o;
+    if (opt) o = *opt; else fmm_options_default(&o);
+    size_t need = 0;
+    {
+        fmm_batched_s tmp;
+        if ((s = batched_build(&tmp, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, o, nullptr, &need)) != FMM_OK)
+            return s;
+    }
+    if (workspace_needed) *workspace_needed = need;
+    if (!out) return FMM_OK;
+    DeviceInfo di;
+    if ((s = device_info(&di)) != FMM_OK) return s;
+    if (count > 0 && (!A || !B || !C)) return FMM_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < need) return FMM_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return FMM_ERR_ALIGNMENT;
+    fmm_batched_s* b = new (std::nothrow) fmm_batched_s();
+    if (!b) return FMM_ERR_OOM;
+    b->num_sms = di.num_sms;
+    if ((s = batched_build(b, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, o, static_cast<char*>(workspace),
+                           nullptr)) != FMM_OK) {
+        delete b;
+        return s;
+    }
+    for (auto* q : b->subs) q->num_sms = di.num_sms;
+    *out = b;
+    return FMM_OK;
+}
+
+fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
+    if (!b) return FMM_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    fmm_status_t s;
+    if (b->njobs > 0) {
+        FMM_CUDA(launch_batched_copy(b->d_jobs, b->njobs, b->job_tiles, stream));
+        b->launches += 1;
+    }
+    for (size_t j = 0; j < b->subs.size(); ++j) {
+        const int i = b->sub_problem[j];
+        if ((s = winograd_pre(b->subs[j], b->A[i], b->B[i], stream)) != FMM_OK) return s;
+    }
+    if (b->total_tiles > 0) {
+        GemmArgs args;
+        memset(&args, 0, sizeof(args));
+        args.ext_maps = b->d_maps;
+        args.ext_groups = b->d_groups;
+        args.num_groups = b->num_groups;
+        args.total_tiles = b->total_tiles;
+        args.raster_m = 16;
+        args.status = b->status;
+        FMM_CUDA(launch_leaf_gemm(args, b->mode, b->bn, b->num_sms, stream));
+        b->launches += 1;
+    }
+    for (size_t j = 0; j < b->subs.size(); ++j) {
+        const int i = b->sub_problem[j];
+        if ((s = winograd_post(b->subs[j], b->alpha[i], b->beta[i], b->C[i], stream)) != FMM_OK) return s;
+    }
+    for (int i = 0; i < b->count; ++i)
+        if (b->scale_only[i] && b->M[i] > 0 && b->N[i] > 0) {
+            FMM_CUDA(launch_scale(b->C[i], b->ldc[i], b->M[i], b->N[i], b->beta[i], stream));
+            b->launches += 1;
+        }
+    for (auto* q : b->subs) { b->launches += q->launches; q->launches = 0; }
+    return FMM_OK;
+}
+
+void fmm_batched_free(fmm_batched_t b) { delete b; }
+
+fmm_status_t fmm_batched_info(fmm_batched_t b, int* depths, int64_t* total_tiles, int64_t* launches) {
+    if (!b) return FMM_ERR_INVALID_ARG;
+    if (depths) for (int i = 0; i < b->count; ++i) depths[i] = b->depth[i];
+    if (total_tiles) *total_tiles = b->total_tiles;
+    if (launches) *launches = b->launches;
+    return FMM_OK;
+}
 
 fmm_status_t fmm_options_default(fmm_options_t* o) {
     if (!o) return FMM_ERR_INVALID_ARG;
@@ -455,6 +798,11 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
     tmp.opt = o;
     tmp.depth = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
     if (M == 0 || N == 0 || K == 0) tmp.depth = 0;
+    tmp.peel = (o.odd == FMM_ODD_PEEL) ? 1 : 0;
+    if (tmp.peel && tmp.depth > 0) {
+        const long long g = 4LL << tmp.depth;
+        if (M / g == 0 || N / g == 0 || K / g == 0) tmp.depth = 0;  // no even core: classical leaf
+    }
     tmp.bn = o.leaf_tile ? o.leaf_tile : 256;
     tmp.mode = (o.precision == FMM_PREC_TF32) ? kLeafTF32 : kLeaf3xTF32;
     size_t need = 0;
@@ -538,9 +886,15 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
                               const int64_t* lda, const float* const* B, const int64_t* ldb, float* const* C,
                               const int64_t* ldc, const float* alpha, const float* beta, const fmm_options_t* opt,
                               void* workspace, size_t workspace_bytes, size_t* workspace_needed, fmm_stream_t stream) {
-    (void)count; (void)M; (void)N; (void)K; (void)A; (void)lda; (void)B; (void)ldb; (void)C; (void)ldc;
-    (void)alpha; (void)beta; (void)opt; (void)workspace; (void)workspace_bytes; (void)workspace_needed; (void)stream;
-    return FMM_ERR_UNSUPPORTED;
+    if (!workspace) return fmm_batched_plan(nullptr, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, opt, nullptr,
+                                            0, workspace_needed, stream);
+    fmm_batched_t b = nullptr;
+    fmm_status_t s = fmm_batched_plan(&b, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, opt, workspace,
+                                      workspace_bytes, workspace_needed, stream);
+    if (s != FMM_OK) return s;
+    s = fmm_batched_run(b, stream);
+    fmm_batched_free(b);  // device tables live in the caller's workspace; host state is not needed after launch
+    return s;
 }
 
 void fmm_free(fmm_plan_t p) {

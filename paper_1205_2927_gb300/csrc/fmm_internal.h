@@ -91,6 +91,21 @@ cudaError_t launch_transpose(const float* B, long long ldb, long long K, long lo
 // Plain copy of an M x K matrix into a buffer with another leading dimension.
 cudaError_t launch_copy2d(const float* A, long long lda, long long M, long long K, float* dst, long long ldd,
                           cudaStream_t stream);
+// Batched copies for many problems in one launch: transpose = 1 writes
+// src^T (src: rows x cols, row stride lds) into dst (cols x rows, row stride
+// ldd); transpose = 0 copies src into dst with another row stride.  32 x 32
+// tiles; tile_begin is the job's first tile in the launch.
+struct CopyJob {
+    const float* src;
+    long long lds;
+    long long rows, cols;
+    float* dst;
+    long long ldd;
+    long long tile_begin;
+    int tiles_c;
+    int transpose;
+};
+cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, long long total_tiles, cudaStream_t stream);
 // C <- beta * C (beta == 0 writes zeros).
 cudaError_t launch_scale(float* C, long long ldc, long long M, long long N, float beta, cudaStream_t stream);
 

@@ -280,8 +280,17 @@ template <int BN, int MODE>
 static cudaError_t launch_impl(const GemmArgs& args, int num_sms, cudaStream_t stream) {
     using Cfg = LeafCfg<BN, MODE>;
     auto kern = leaf_gemm_kernel<BN, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    // once per device and instantiation (keeps later launches free of other API
+    // calls, e.g. while a stream is being captured into a CUDA graph)
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
     if (args.total_tiles <= 0) return cudaSuccess;
     const long long grid = args.total_tiles < num_sms ? args.total_tiles : num_sms;
     kern<<<(unsigned)grid, Cfg::kThreads, Cfg::kSmem, stream>>>(args);

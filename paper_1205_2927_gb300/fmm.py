@@ -212,3 +212,74 @@ def matmul(A, B, depth=-1, precision="fp32", **kw):
     N = B.shape[1]
     p = Plan(M, N, K, A.stride(0), B.stride(0), N, depth=depth, precision=precision, **kw)
     return p(A, B)
+
+
+# ------------------------------------------------------------------ batched
+
+def _batched_argtypes():
+    i64p, vpp = C.POINTER(C.c_int64), C.POINTER(C.c_void_p)
+    fp = C.POINTER(C.c_float)
+    common = [C.c_int, i64p, i64p, i64p, vpp, i64p, vpp, i64p, vpp, i64p, fp, fp, C.POINTER(Options),
+              C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t), C.c_void_p]
+    _lib.fmm_batched_plan.argtypes = [C.POINTER(C.c_void_p)] + common
+    _lib.fmm_batched_plan.restype = C.c_int
+    _lib.fmm_batched_run.argtypes = [C.c_void_p, C.c_void_p]
+    _lib.fmm_batched_run.restype = C.c_int
+    _lib.fmm_batched_free.argtypes = [C.c_void_p]
+    _lib.fmm_batched_free.restype = None
+    _lib.fmm_batched_info.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    _lib.fmm_batched_info.restype = C.c_int
+
+
+_batched_argtypes()
+
+
+class BatchedPlan:
+    """Batched products C_i = alpha_i A_i B_i + beta_i C_i over lists of 2-D float32
+    CUDA tensors (row-major, unit column stride).  run() only launches kernels,
+    so it can be captured in a CUDA graph."""
+
+    def __init__(self, As, Bs, Cs, alpha=1.0, beta=0.0, stream=None, **opt_kwargs):
+        import torch
+        n = len(As)
+        self.count = n
+        self._keep = (list(As), list(Bs), list(Cs))
+        i64 = C.c_int64 * n
+        vp = C.c_void_p * n
+        f = C.c_float * n
+        al = [alpha] * n if not isinstance(alpha, (list, tuple)) else alpha
+        be = [beta] * n if not isinstance(beta, (list, tuple)) else beta
+        self._arrs = (i64(*[a.shape[0] for a in As]), i64(*[b.shape[1] for b in Bs]), i64(*[a.shape[1] for a in As]),
+                      vp(*[a.data_ptr() for a in As]), i64(*[max(a.stride(0), 1) for a in As]),
+                      vp(*[b.data_ptr() for b in Bs]), i64(*[max(b.stride(0), 1) for b in Bs]),
+                      vp(*[c.data_ptr() for c in Cs]), i64(*[max(c.stride(0), 1) for c in Cs]),
+                      f(*al), f(*be))
+        self.opt = options(**opt_kwargs)
+        need = C.c_size_t(0)
+        _check(_lib.fmm_batched_plan(None, n, *self._arrs, C.byref(self.opt), None, 0, C.byref(need), None),
+               "fmm_batched_plan(query)")
+        self.workspace = torch.empty(max(need.value, 256), dtype=torch.uint8, device=As[0].device if n else "cuda")
+        self.handle = C.c_void_p()
+        _check(_lib.fmm_batched_plan(C.byref(self.handle), n, *self._arrs, C.byref(self.opt),
+                                     C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(), C.byref(need),
+                                     _stream_ptr(stream)), "fmm_batched_plan")
+
+    def run(self, stream=None):
+        _check(_lib.fmm_batched_run(self.handle, _stream_ptr(stream)), "fmm_batched_run")
+
+    def info(self):
+        d = (C.c_int * max(self.count, 1))()
+        t, l = C.c_int64(), C.c_int64()
+        _check(_lib.fmm_batched_info(self.handle, d, C.byref(t), C.byref(l)), "fmm_batched_info")
+        return dict(depths=list(d)[: self.count], total_tiles=t.value, launches=l.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.fmm_batched_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

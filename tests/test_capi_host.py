@@ -102,3 +102,12 @@ def test_no_cpu_fallback_without_gpu(F):
     st = F.library().fmm_plan(C.byref(h), 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None)
     assert st == 8  # FMM_ERR_NO_DEVICE
     assert not h.value
+
+
+def test_peel_workspace_has_no_padding(F):
+    # peel: the recursion covers the even core only; pad rounds the sizes up
+    s_peel = _query(F, 1000, 1000, 1000, depth=3, odd="peel")
+    s_pad = _query(F, 1000, 1000, 1000, depth=3, odd="pad")
+    s_core = _query(F, 992, 992, 992, depth=3, odd="pad")
+    assert s_peel > s_core        # core buffers + transposed B and aligned A for the border
+    assert s_pad > s_core         # 1000 -> 1024

@@ -160,3 +160,65 @@ def test_strided_operands(fmm):
         assert np.array_equal(got[:, :n], ref)
         assert np.all(got[:, n:] == 0)
         p.close()
+
+
+# --- odd sizes: peeling ------------------------------------------------------
+
+@pytest.mark.parametrize("m,k,n,d", [(300, 200, 260, 2), (1000, 1000, 1000, 3), (517, 133, 389, 1), (20, 40, 60, 3)])
+def test_peel_bit_exact_small_int(fmm, m, k, n, d):
+    A = I.small_int((m, k), 5000 + m, r=2)
+    B = I.small_int((k, n), 6000 + n, r=2)
+    C, info = run(fmm, A, B, depth=d, odd="peel")
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(O.winograd(A, B, d, "peel"), ref)
+    assert np.array_equal(C, ref)
+
+
+@pytest.mark.parametrize("odd", ["pad", "peel"])
+def test_odd_size_error_bound(fmm, odd):
+    m = k = n = 1187  # odd at every level
+    A, B = I.operands(m, k, n, I.seed_for(2, 3))
+    C, _ = run(fmm, A, B, depth=3, odd=odd)
+    assert O.error_metric(C, O.classical(A, B), A, B) <= FP32_BOUND
+
+
+def test_peel_blas_semantics(fmm):
+    m, k, n = 290, 150, 330
+    A = I.small_int((m, k), 15, r=3)
+    B = I.small_int((k, n), 16, r=3)
+    C0 = I.small_int((m, n), 17, r=5)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
+    C, _ = run(fmm, A, B, C0, alpha=2.0, beta=-1.0, depth=2, odd="peel")
+    assert np.array_equal(C, (2.0 * ref - C0).astype(np.float32))
+
+
+# --- residual check ------------------------------------------------------------
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64):
+    import ctypes
+    import torch
+    m, k, n = 700, 500, 600
+    A = I.small_int((m, k), 21, r=3)
+    B = I.small_int((k, n), 22, r=3)
+    Cx = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    Cx[123, 45] += 1.0
+    x = I.rademacher(n, 23)
+    dA, dB, dC, dx = (torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in (A, B, Cx, x))
+    r = torch.empty(m, dtype=torch.float64, device="cuda")
+    need = ctypes.c_size_t(0)
+    lib = fmm.library()
+    lib.fmm_residual.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64] * 3 + \
+        [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+         ctypes.c_int, ctypes.c_void_p]
+    assert lib.fmm_residual(m, n, k, None, k, None, n, None, n, None, None, None, 0, ctypes.byref(need), 0, None) == 0
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    st = lib.fmm_residual(m, n, k, dA.data_ptr(), k, dB.data_ptr(), n, dC.data_ptr(), n, dx.data_ptr(),
+                          r.data_ptr(), ws.data_ptr(), need.value, None, fp64,
+                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    got = r.cpu().numpy()
+    want = O.freivalds(A, B, Cx, x)
+    assert np.array_equal(got, want)           # integer data: exact in both accumulations
+    assert np.count_nonzero(got) == 1 and abs(got[123]) == 1.0
