@@ -188,6 +188,60 @@ fmm_status_t fmm_residual(int64_t M, int64_t N, int64_t K, const float* A, int64
                           const float* x, double* r, void* workspace, size_t workspace_bytes,
                           size_t* workspace_needed, int fp64, fmm_stream_t stream);
 
+/* ---------------------------------------------------------------- planner
+ * Candidate plans of a problem: depth 0..4 (a level only while every leaf
+ * dimension stays >= 128) x leaf tile {128, 256}, restricted by opt->depth /
+ * opt->leaf_tile when those are set.  The reviewer critique of the paper's
+ * fixed thresholds (Table 2, recursion point of Sec. 3.1) is that they never
+ * ask whether one more split would pay; these planners do.
+ *
+ * fmm_autotune times every candidate on the caller's device buffers A, B, C
+ * (C is overwritten) with CUDA events on `stream` (1 warm-up + reps timed
+ * runs, median) and synchronises.  depths/tiles/times_ms receive up to 16
+ * entries, *count their number; any may be NULL.  workspace: at least
+ * *workspace_needed bytes (the largest candidate); with workspace == NULL
+ * only *workspace_needed is set. */
+fmm_status_t fmm_autotune(int64_t M, int64_t N, int64_t K, const fmm_options_t* opt,
+                          const float* A, const float* B, float* C,
+                          void* workspace, size_t workspace_bytes, size_t* workspace_needed,
+                          int* depths, int* tiles, float* times_ms, int* count, int reps,
+                          fmm_stream_t stream);
+
+/* Cost-model network used by FMM_PLANNER_MLP: 6 -> 64 -> 64 -> 1, ReLU, fp32,
+ * FMM_MLP_NPARAM parameters laid out W1[64][6], b1[64], W2[64][64], b2[64],
+ * W3[1][64], b3[1] (weights row-major [out][in]).  Input features of a
+ * candidate (see fmm_plan_features) are standardised with the given mean and
+ * std (6 floats each); the output predicts log(milliseconds). */
+#define FMM_MLP_NPARAM 4673
+
+/* Raw features of a candidate: log2 M, log2 K, log2 N, depth, leaf_tile/128,
+ * precision id.  Host only. */
+fmm_status_t fmm_plan_features(int64_t M, int64_t N, int64_t K, int depth, int leaf_tile, int precision,
+                               float* out6);
+
+/* Network inference: Y[i] = f(X[i, 0:6]) for `batch` standardised feature
+ * rows.  params, X, Y: device pointers.  Asynchronous, one launch. */
+fmm_status_t fmm_mlp_forward(const float* params, const float* X, float* Y, int batch, fmm_stream_t stream);
+
+/* One full-batch training step of 0.5 * mean((f(X) - T)^2) with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; `step` counts from 1;
+ * lr == 0 computes gradients without updating).  params, adam_m, adam_v:
+ * FMM_MLP_NPARAM device floats each, updated in place.  grad_out (nullable,
+ * FMM_MLP_NPARAM device floats) receives the gradient; loss_out (nullable,
+ * one device float) the loss before the update.  workspace: device memory,
+ * *workspace_needed bytes (activations of the batch); with workspace and
+ * params NULL only the size is returned.  Deterministic summation order. */
+fmm_status_t fmm_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr,
+                                const float* X, const float* T, int batch,
+                                void* workspace, size_t workspace_bytes, size_t* workspace_needed,
+                                float* grad_out, float* loss_out, fmm_stream_t stream);
+
+/* Register the cost model for FMM_PLANNER_MLP (host pointers, copied).  The
+ * parameters are uploaded to each device on first use.  params == NULL
+ * unregisters; without a model FMM_PLANNER_MLP falls back to the exhaustive
+ * autotuner. */
+fmm_status_t fmm_set_cost_model(const float* params, const float* mean6, const float* std6);
+
 /* Phase profiling.  fmm_plan_profile(plan, 1) resets the counters and makes
  * every later fmm_gemm on the plan record CUDA events (on the call's stream)
  * around three phases: pre-additions (plus operand copies), the leaf launch,

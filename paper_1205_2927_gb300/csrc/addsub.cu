@@ -278,6 +278,39 @@ __global__ void __launch_bounds__(256) batched_copy_kernel(const CopyJob* __rest
     }
 }
 
+__global__ void fill_kernel(float* p, size_t n, unsigned seed) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned x = (unsigned)i * 2654435761u ^ seed;   // integer hash (xorshift-multiply)
+        x ^= x >> 16; x *= 0x7feb352du; x ^= x >> 15; x *= 0x846ca68bu; x ^= x >> 16;
+        p[i] = (float)(x >> 8) * (2.0f / 16777216.0f) - 1.0f;
+    }
+}
+
+// max |x| over a rows x cols matrix, folded into *out (float bits; non-negative
+// floats order like unsigned integers)
+__global__ void absmax_kernel(const float* __restrict__ X, long long ld, long long rows, long long cols,
+                              unsigned* out) {
+    float m = 0.f;
+    for (long long r = blockIdx.y; r < rows; r += gridDim.y)
+        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (long long)gridDim.x * blockDim.x)
+            m = fmaxf(m, fabsf(X[r * ld + c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void fp16_scale_kernel(const unsigned* mx, float bound_mult, float* scale) {
+    const int i = threadIdx.x;
+    if (i > 1) return;
+    const float m = __uint_as_float(mx[i]) * bound_mult;
+    if (!(m > 0.f) || !isfinite(m)) { scale[i] = 1.0f; return; }
+    int x;
+    frexpf(m, &x);                   // m = f * 2^x, 0.5 <= f < 1
+    int e = 14 - x;                  // largest e with m * 2^e <= 2^14
+    e = max(-100, min(100, e));
+    scale[i] = ldexpf(1.0f, e);
+}
+
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -349,6 +382,23 @@ cudaError_t launch_copy2d(const float* A, long long lda, long long M, long long 
 cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, long long total_tiles, cudaStream_t stream) {
     if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
     batched_copy_kernel<<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp16_scales(const float* A, long long lda, long long M, long long K, const float* B,
+                               long long ldb, long long N, float bound_mult, float* scale, unsigned* scratch,
+                               cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    if (M > 0 && K > 0) absmax_kernel<<<dim3(4, gy(M < 1024 ? M : 1024)), 256, 0, stream>>>(A, lda, M, K, scratch);
+    if (K > 0 && N > 0) absmax_kernel<<<dim3(4, gy(K < 1024 ? K : 1024)), 256, 0, stream>>>(B, ldb, K, N, scratch + 1);
+    fp16_scale_kernel<<<1, 32, 0, stream>>>(scratch, bound_mult, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    fill_kernel<<<1024, 256, 0, stream>>>(p, n, seed);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -138,6 +139,9 @@ struct fmm_plan_s {
     long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
     int peel = 0;
     float border_beta = 0.f;
+    // FP16x3: device operand scales {s_a, s_b} and reduction scratch, inside the status block
+    float* fp16_scale() const { return reinterpret_cast<float*>(status + 16); }
+    unsigned* fp16_scratch() const { return status + 24; }
     char* ws = nullptr;
     size_t ws_bytes = 0;
     unsigned* status = nullptr;
@@ -257,9 +261,17 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL) return FMM_ERR_INVALID_ARG;
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
-    if (o->precision == FMM_PREC_BF16X3 || o->precision == FMM_PREC_FP16X3) return FMM_ERR_UNSUPPORTED;
     if (o->algo == FMM_ALGO_CLASSICAL || o->host_operands) return FMM_ERR_UNSUPPORTED;
     return FMM_OK;
+}
+
+int leaf_mode(fmm_precision_t p) {
+    switch (p) {
+        case FMM_PREC_TF32: return kLeafTF32;
+        case FMM_PREC_BF16X3: return kLeafBF16x3;
+        case FMM_PREC_FP16X3: return kLeafFP16x3;
+        default: return kLeaf3xTF32;
+    }
 }
 
 // Fixed-threshold planner: one more level while every dimension of the next
@@ -287,6 +299,8 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream) {
     args.raster_m = 16;
     args.ext_maps = nullptr;
     args.ext_groups = nullptr;
+    if (p->mode == kLeafFP16x3)
+        for (int g = 0; g < args.num_groups; ++g) args.groups[g].scale = p->fp16_scale();
     args.status = p->status;
     FMM_CUDA(launch_leaf_gemm(args, p->mode, p->bn, p->num_sms, stream));
     p->launches += args.total_tiles > 0 ? 1 : 0;
@@ -498,6 +512,20 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
     return FMM_OK;
 }
 
+// One multiply with the plan's schedule (FP16x3 first derives its operand scales).
+fmm_status_t execute(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
+                     cudaStream_t stream) {
+    if (p->mode == kLeafFP16x3) {
+        // operand magnitudes of the leaves are bounded by 4^depth times the root's
+        const float bound = (float)(1LL << (2 * p->depth));
+        FMM_CUDA(launch_fp16_scales(A, p->lda, p->M, p->K, B, p->ldb, p->N, bound, p->fp16_scale(),
+                                    p->fp16_scratch(), stream));
+        p->launches += 3;
+    }
+    return (p->depth == 0) ? run_classical(p, alpha, A, B, beta, C, stream)
+                           : run_winograd(p, alpha, A, B, beta, C, stream);
+}
+
 }  // namespace
 
 // ----------------------------------------------------------------------------------------- batched
@@ -536,7 +564,7 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     b->status = cv.take<unsigned>(64);
     b->count = count;
     b->bn = o.leaf_tile ? o.leaf_tile : 256;
-    b->mode = (o.precision == FMM_PREC_TF32) ? kLeafTF32 : kLeaf3xTF32;
+    b->mode = leaf_mode(o.precision);
     // per-problem depth and resource counts
     int total_maps = 0, total_groups = 0, total_jobs = 0;
     b->depth.assign(count, 0);
@@ -655,13 +683,274 @@ fmm_status_t batched_check(int count, const int64_t* M, const int64_t* N, const 
     if (opt) {
         fmm_status_t s = check_opts(opt);
         if (s != FMM_OK) return s;
-        if (opt->odd != FMM_ODD_PAD) return FMM_ERR_UNSUPPORTED;
+        if (opt->odd != FMM_ODD_PAD || opt->precision == FMM_PREC_FP16X3) return FMM_ERR_UNSUPPORTED;
     }
     (void)A; (void)B; (void)C;
     return FMM_OK;
 }
 
 }  // namespace
+
+namespace {
+
+// ----------------------------------------------------------------------------------------- planner
+void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long lda, long long ldb, long long ldc,
+              const fmm_options_t& o, int depth, int bn) {
+    t.M = M; t.N = N; t.K = K; t.lda = lda; t.ldb = ldb; t.ldc = ldc;
+    t.opt = o;
+    t.depth = (M == 0 || N == 0 || K == 0) ? 0 : depth;
+    t.peel = (o.odd == FMM_ODD_PEEL) ? 1 : 0;
+    if (t.peel && t.depth > 0) {
+        const long long g = 4LL << t.depth;
+        if (M / g == 0 || N / g == 0 || K / g == 0) t.depth = 0;  // no even core: classical leaf
+    }
+    t.bn = bn;
+    t.mode = leaf_mode(o.precision);
+}
+
+size_t plan_bytes(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,
+                  const fmm_options_t& o, int depth, int bn) {
+    fmm_plan_s t;
+    make_tmp(t, M, N, K, lda, ldb, ldc, o, depth, bn);
+    size_t need = 0;
+    layout(&t, nullptr, &need);
+    return need;
+}
+
+struct Cand { int depth, bn; };
+
+int candidates(long long M, long long N, long long K, const fmm_options_t& o, Cand* out) {
+    long long mn = std::min(std::min(M, N), K);
+    int n = 0;
+    for (int d = 0; d <= 4; ++d) {
+        if (d > 0 && (mn >> d) < 128) break;
+        if (o.depth >= 0 && d != o.depth) continue;
+        for (int bn : {128, 256}) {
+            if (o.leaf_tile && bn != o.leaf_tile) continue;
+            out[n++] = Cand{d, bn};
+        }
+    }
+    if (n == 0) out[n++] = Cand{o.depth >= 0 ? o.depth : 0, o.leaf_tile ? o.leaf_tile : 256};
+    return n;
+}
+
+struct CostModel {
+    bool set = false;
+    float params[FMM_MLP_NPARAM];
+    float mean[6], stdv[6];
+    float* dev_params[64] = {};
+    float* dev_io[64] = {};   // 16 x 6 features + 16 outputs
+    int version = 0;
+    int dev_version[64] = {};
+};
+CostModel g_model;
+
+void raw_features(long long M, long long N, long long K, int depth, int bn, int prec, float* f) {
+    f[0] = (float)std::log2((double)std::max(M, 1LL));
+    f[1] = (float)std::log2((double)std::max(K, 1LL));
+    f[2] = (float)std::log2((double)std::max(N, 1LL));
+    f[3] = (float)depth;
+    f[4] = (float)bn / 128.0f;
+    f[5] = (float)prec;
+}
+
+// Score the candidates with the registered network (one inference launch) and
+// return the index of the smallest predicted time (ties: smaller depth, then
+// the larger tile).
+fmm_status_t choose_mlp(long long M, long long N, long long K, const fmm_options_t& o, const Cand* c, int n,
+                        int* best, cudaStream_t stream) {
+    int dev = 0;
+    FMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return FMM_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_model.dev_params[dev]) {
+        FMM_CUDA(cudaMalloc(&g_model.dev_params[dev], sizeof(float) * FMM_MLP_NPARAM));
+        FMM_CUDA(cudaMalloc(&g_model.dev_io[dev], sizeof(float) * (16 * 6 + 16)));
+    }
+    if (g_model.dev_version[dev] != g_model.version) {
+        FMM_CUDA(cudaMemcpy(g_model.dev_params[dev], g_model.params, sizeof(float) * FMM_MLP_NPARAM,
+                            cudaMemcpyHostToDevice));
+        g_model.dev_version[dev] = g_model.version;
+    }
+    float X[16 * 6], Y[16];
+    for (int i = 0; i < n; ++i) {
+        raw_features(M, N, K, c[i].depth, c[i].bn, (int)o.precision, X + 6 * i);
+        for (int j = 0; j < 6; ++j) X[6 * i + j] = (X[6 * i + j] - g_model.mean[j]) / g_model.stdv[j];
+    }
+    float* dX = g_model.dev_io[dev];
+    float* dY = dX + 16 * 6;
+    FMM_CUDA(cudaMemcpyAsync(dX, X, sizeof(float) * 6 * n, cudaMemcpyHostToDevice, stream));
+    FMM_CUDA(mlp_forward(g_model.dev_params[dev], dX, dY, n, stream));
+    FMM_CUDA(cudaMemcpyAsync(Y, dY, sizeof(float) * n, cudaMemcpyDeviceToHost, stream));
+    FMM_CUDA(cudaStreamSynchronize(stream));
+    int b = 0;
+    for (int i = 1; i < n; ++i) {
+        const float d = Y[i] - Y[b];
+        if (d < -1e-6f) b = i;
+        else if (d <= 1e-6f && (c[i].depth < c[b].depth || (c[i].depth == c[b].depth && c[i].bn > c[b].bn))) b = i;
+    }
+    *best = b;
+    return FMM_OK;
+}
+
+// Time each candidate on A, B, C (dense row-major) with the workspace `ws`.
+fmm_status_t autotune_core(long long M, long long N, long long K, const fmm_options_t& o, const float* A,
+                           const float* B, float* C, char* ws, size_t ws_bytes, const Cand* c, int n, int reps,
+                           float* times, cudaStream_t stream) {
+    DeviceInfo di;
+    fmm_status_t s;
+    if ((s = device_info(&di)) != FMM_OK) return s;
+    cudaEvent_t e0, e1;
+    FMM_CUDA(cudaEventCreate(&e0));
+    FMM_CUDA(cudaEventCreate(&e1));
+    s = FMM_OK;
+    for (int i = 0; i < n && s == FMM_OK; ++i) {
+        fmm_plan_s t;
+        make_tmp(t, M, N, K, K, N, N, o, c[i].depth, c[i].bn);
+        size_t need = 0;
+        layout(&t, nullptr, &need);
+        if (need > ws_bytes) { s = FMM_ERR_WORKSPACE; break; }
+        layout(&t, ws, nullptr);
+        t.ws = ws;
+        t.ws_bytes = ws_bytes;
+        t.num_sms = di.num_sms;
+        std::vector<float> ms;
+        for (int r = 0; r <= reps && s == FMM_OK; ++r) {
+            cudaEventRecord(e0, stream);
+            s = execute(&t, 1.f, A, B, 0.f, C, stream);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { s = cuda_fail(cudaGetLastError(), "autotune"); break; }
+            float x = 0.f;
+            cudaEventElapsedTime(&x, e0, e1);
+            if (r > 0) ms.push_back(x);
+        }
+        if (s != FMM_OK) break;
+        std::sort(ms.begin(), ms.end());
+        times[i] = ms.empty() ? 0.f : ms[ms.size() / 2];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+}
+
+size_t scratch_bytes(long long M, long long N, long long K) {
+    return align_up((size_t)M * K * 4, 256) + align_up((size_t)K * N * 4, 256) + align_up((size_t)M * N * 4, 256);
+}
+
+// Choose (depth, leaf tile) for a plan and the workspace bytes it needs.
+fmm_status_t plan_choose(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,
+                         const fmm_options_t& o, void* ws, size_t ws_bytes, size_t* need, int& depth, int& bn,
+                         cudaStream_t stream, bool query) {
+    if (o.planner == FMM_PLANNER_FIXED || M == 0 || N == 0 || K == 0) {
+        depth = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
+        bn = o.leaf_tile ? o.leaf_tile : 256;
+        *need = plan_bytes(M, N, K, lda, ldb, ldc, o, depth, bn);
+        return FMM_OK;
+    }
+    Cand c[16];
+    const int n = candidates(M, N, K, o, c);
+    if (o.planner == FMM_PLANNER_MLP && g_model.set) {
+        int b = 0;
+        fmm_status_t s = choose_mlp(M, N, K, o, c, n, &b, stream);
+        if (s != FMM_OK) return s;
+        depth = c[b].depth;
+        bn = c[b].bn;
+        *need = plan_bytes(M, N, K, lda, ldb, ldc, o, depth, bn);
+        return FMM_OK;
+    }
+    // exhaustive (also the fallback of the learned planner): the largest
+    // candidate plus scratch operands for the timing runs
+    size_t mx = 0;
+    for (int i = 0; i < n; ++i) {
+        fmm_plan_s t;
+        make_tmp(t, M, N, K, K, N, N, o, c[i].depth, c[i].bn);
+        size_t q = 0;
+        layout(&t, nullptr, &q);
+        mx = std::max(mx, q);
+        mx = std::max(mx, plan_bytes(M, N, K, lda, ldb, ldc, o, c[i].depth, c[i].bn));
+    }
+    *need = align_up(mx, 256) + scratch_bytes(M, N, K);
+    depth = c[0].depth;
+    bn = c[0].bn;
+    if (query) return FMM_OK;
+    if (!ws || ws_bytes < *need) return FMM_ERR_WORKSPACE;
+    char* base = static_cast<char*>(ws);
+    float* sA = reinterpret_cast<float*>(base + align_up(mx, 256));
+    float* sB = reinterpret_cast<float*>(reinterpret_cast<char*>(sA) + align_up((size_t)M * K * 4, 256));
+    float* sC = reinterpret_cast<float*>(reinterpret_cast<char*>(sB) + align_up((size_t)K * N * 4, 256));
+    FMM_CUDA(launch_fill(sA, (size_t)M * K, 12345u, stream));
+    FMM_CUDA(launch_fill(sB, (size_t)K * N, 54321u, stream));
+    float times[16];
+    fmm_status_t s = autotune_core(M, N, K, o, sA, sB, sC, base, align_up(mx, 256), c, n, 1, times, stream);
+    if (s != FMM_OK) return s;
+    int b = 0;
+    for (int i = 1; i < n; ++i)
+        if (times[i] < times[b]) b = i;
+    depth = c[b].depth;
+    bn = c[b].bn;
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm_status_t fmm_plan_features(int64_t M, int64_t N, int64_t K, int depth, int leaf_tile, int precision,
+                               float* out6) {
+    if (!out6 || M < 0 || N < 0 || K < 0) return FMM_ERR_INVALID_ARG;
+    raw_features(M, N, K, depth, leaf_tile, precision, out6);
+    return FMM_OK;
+}
+
+fmm_status_t fmm_set_cost_model(const float* params, const float* mean6, const float* std6) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!params) {
+        g_model.set = false;
+        return FMM_OK;
+    }
+    if (!mean6 || !std6) return FMM_ERR_INVALID_ARG;
+    for (int j = 0; j < 6; ++j)
+        if (!(std6[j] > 0.f)) return FMM_ERR_INVALID_ARG;
+    memcpy(g_model.params, params, sizeof(g_model.params));
+    memcpy(g_model.mean, mean6, sizeof(g_model.mean));
+    memcpy(g_model.stdv, std6, sizeof(g_model.stdv));
+    g_model.set = true;
+    g_model.version += 1;
+    return FMM_OK;
+}
+
+fmm_status_t fmm_autotune(int64_t M, int64_t N, int64_t K, const fmm_options_t* opt, const float* A, const float* B,
+                          float* C, void* workspace, size_t workspace_bytes, size_t* workspace_needed, int* depths,
+                          int* tiles, float* times_ms, int* count, int reps, fmm_stream_t stream) {
+    if (M <= 0 || N <= 0 || K <= 0 || reps < 1) return FMM_ERR_INVALID_ARG;
+    fmm_options_t o;
+    if (opt) o = *opt; else fmm_options_default(&o);
+    fmm_status_t s = check_opts(&o);
+    if (s != FMM_OK) return s;
+    Cand c[16];
+    const int n = candidates(M, N, K, o, c);
+    size_t mx = 0;
+    for (int i = 0; i < n; ++i) mx = std::max(mx, plan_bytes(M, N, K, K, N, N, o, c[i].depth, c[i].bn));
+    if (workspace_needed) *workspace_needed = mx;
+    if (count) *count = n;
+    for (int i = 0; i < n; ++i) {
+        if (depths) depths[i] = c[i].depth;
+        if (tiles) tiles[i] = c[i].bn;
+    }
+    if (!workspace) return FMM_OK;
+    if (!A || !B || !C) return FMM_ERR_INVALID_ARG;
+    if (workspace_bytes < mx) return FMM_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return FMM_ERR_ALIGNMENT;
+    float t[16];
+    s = autotune_core(M, N, K, o, A, B, C, static_cast<char*>(workspace), workspace_bytes, c, n, reps, t,
+                      (cudaStream_t)stream);
+    if (s != FMM_OK) return s;
+    if (times_ms)
+        for (int i = 0; i < n; ++i) times_ms[i] = t[i];
+    return FMM_OK;
+}
+
+}  // extern "C"
 
 extern "C" {
 
@@ -793,20 +1082,15 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
     if (opt) o = *opt; else fmm_options_default(&o);
     fmm_status_t s = check_opts(&o);
     if (s != FMM_OK) return s;
-    fmm_plan_s tmp;
-    tmp.M = M; tmp.N = N; tmp.K = K; tmp.lda = lda; tmp.ldb = ldb; tmp.ldc = ldc;
-    tmp.opt = o;
-    tmp.depth = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
-    if (M == 0 || N == 0 || K == 0) tmp.depth = 0;
-    tmp.peel = (o.odd == FMM_ODD_PEEL) ? 1 : 0;
-    if (tmp.peel && tmp.depth > 0) {
-        const long long g = 4LL << tmp.depth;
-        if (M / g == 0 || N / g == 0 || K / g == 0) tmp.depth = 0;  // no even core: classical leaf
-    }
-    tmp.bn = o.leaf_tile ? o.leaf_tile : 256;
-    tmp.mode = (o.precision == FMM_PREC_TF32) ? kLeafTF32 : kLeaf3xTF32;
+    int depth = 0, bn = 256;
     size_t need = 0;
-    layout(&tmp, nullptr, &need);
+    // the planner may time candidates on scratch operands carved from the workspace
+    const bool ws_ok = workspace && !(reinterpret_cast<uintptr_t>(workspace) & 255);
+    if ((s = plan_choose(M, N, K, lda, ldb, ldc, o, ws_ok ? workspace : nullptr, workspace_bytes, &need, depth, bn,
+                         (cudaStream_t)stream, out == nullptr)) != FMM_OK)
+        return s;
+    fmm_plan_s tmp;
+    make_tmp(tmp, M, N, K, lda, ldb, ldc, o, depth, bn);
     if (workspace_needed) *workspace_needed = need;
     if (!out) return FMM_OK;
     DeviceInfo di;
@@ -849,8 +1133,7 @@ fmm_status_t fmm_gemm(fmm_plan_t p, float alpha, const float* A, const float* B,
         p->cur = &es;
         mark(p, 0, stream);
     }
-    fmm_status_t st = (p->depth == 0) ? run_classical(p, alpha, A, B, beta, C, stream)
-                                      : run_winograd(p, alpha, A, B, beta, C, stream);
+    fmm_status_t st = execute(p, alpha, A, B, beta, C, stream);
     p->calls += 1;
     if (p->cur) {
         mark(p, 3, stream);

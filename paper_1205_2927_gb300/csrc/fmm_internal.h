@@ -30,6 +30,7 @@ struct GemmGroup {
     int a_batch_off, b_batch_off;
     int vec_ok;             // C, ldc and the batch stride allow 16-byte stores
     int pad_;
+    const float* scale;     // 16-bit split leaves: device {s_a, s_b} power-of-two operand scales, or null
 };
 
 struct GemmArgs {
@@ -44,7 +45,7 @@ struct GemmArgs {
 };
 
 // precision of a leaf launch
-enum LeafMode : int { kLeafTF32 = 0, kLeaf3xTF32 = 1 };
+enum LeafMode : int { kLeafTF32 = 0, kLeaf3xTF32 = 1, kLeafBF16x3 = 2, kLeafFP16x3 = 3 };
 
 // Launch the persistent tensor-core leaf kernel.  Returns a cudaError_t.
 cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms, cudaStream_t stream);
@@ -106,6 +107,16 @@ struct CopyJob {
     int transpose;
 };
 cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, long long total_tiles, cudaStream_t stream);
+// FP16x3 operand scales: scale[0] = 2^e_a, scale[1] = 2^e_b with the largest
+// e such that bound_mult * max|X| * 2^e <= 2^14 (1 when X is all zero); the
+// maxima are taken over the M x K / K x N operands (any leading dimension).
+cudaError_t launch_fp16_scales(const float* A, long long lda, long long M, long long K, const float* B,
+                               long long ldb, long long N, float bound_mult, float* scale, unsigned* scratch,
+                               cudaStream_t stream);
+// Deterministic pseudo-random fill of n floats in [-1, 1) (autotuner scratch).
+cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream);
+// Cost-model inference (mlp.cu): Y = f(X), `batch` rows of 6 features.
+cudaError_t mlp_forward(const float* params, const float* X, float* Y, int batch, cudaStream_t s);
 // C <- beta * C (beta == 0 writes zeros).
 cudaError_t launch_scale(float* C, long long ldc, long long M, long long N, float beta, cudaStream_t stream);
 

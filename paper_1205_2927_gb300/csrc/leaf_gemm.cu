@@ -23,6 +23,9 @@
 #include "fmm_internal.h"
 #include "ptx.cuh"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace fmm {
 
 template <int BN, int MODE>
@@ -31,15 +34,37 @@ struct LeafCfg {
     static constexpr int kABytes = kBM * 128;
     static constexpr int kBBytes = BN * 128;
     static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr int kLoBytes = (MODE == kLeaf3xTF32) ? kStageBytes : 0;
+    static constexpr bool kSplit = MODE != kLeafTF32;   // split warps + a second buffer per stage
+    static constexpr bool k16 = MODE == kLeafBF16x3 || MODE == kLeafFP16x3;
+    static constexpr int kLoBytes = kSplit ? kStageBytes : 0;
     static constexpr int kTmemCols = 2 * BN;
-    static constexpr int kThreads = (MODE == kLeaf3xTF32) ? 384 : 256;
+    static constexpr int kThreads = kSplit ? 384 : 256;
     static constexpr int kBarBytes = 256;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kStageBytes + kLoBytes) + kBarBytes;
     static_assert((3 * kStages + 4) * 8 + 16 <= kBarBytes, "barrier area");
     static_assert(kSmem <= 227 * 1024, "shared memory");
     static_assert(kTmemCols == 256 || kTmemCols == 512, "TMEM columns");
 };
+
+// hi = rn16(x), lo = rn16(x - hi) for four values, packed as 4 x 16 bits.
+template <bool BF16>
+__device__ __forceinline__ void split16(float x0, float x1, float x2, float x3, uint2& hi, uint2& lo) {
+    if constexpr (BF16) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1), h23 = __floats2bfloat162_rn(x2, x3);
+        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - f01.x, x1 - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - f23.x, x3 - f23.y);
+        hi = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        lo = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+    } else {
+        const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
+        const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+        const __half2 l01 = __floats2half2_rn(x0 - f01.x, x1 - f01.y);
+        const __half2 l23 = __floats2half2_rn(x2 - f23.x, x3 - f23.y);
+        hi = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+        lo = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+    }
+}
 
 __device__ __forceinline__ void decode_tile(const GemmGroup* groups, int ng, int raster_m, long long t, int& g,
                                             int& b, int& tm, int& tn) {
@@ -138,6 +163,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = make_idesc(2u, kBM, BN);
+            constexpr uint32_t idesc16 = make_idesc(MODE == kLeafBF16x3 ? 1u : 0u, kBM, BN);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -151,11 +177,30 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < nk; ++kb) {
-                    const uint32_t wb = (MODE == kLeaf3xTF32) ? ready_bar(stage) : full_bar(stage);
+                    const uint32_t wb = Cfg::kSplit ? ready_bar(stage) : full_bar(stage);
                     if (!mbar_wait(wb, phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
                     const uint32_t sb = sa + Cfg::kABytes;
+                    if constexpr (Cfg::k16) {
+                        // 16-bit hi/lo tiles, 64-byte rows: A hi | B hi | A lo | B lo
+                        const uint32_t ah = lo0 + stage * Cfg::kStageBytes;
+                        const uint32_t bh = ah + kBM * 64;
+                        const uint32_t al = bh + BN * 64;
+                        const uint32_t bl = al + kBM * 64;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                            const uint64_t ahd = sdesc_kmajor_sw64(ah + kk * 32);
+                            const uint64_t bhd = sdesc_kmajor_sw64(bh + kk * 32);
+                            mma_f16(d, sdesc_kmajor_sw64(al + kk * 32), bhd, idesc16, first);  // lo_a * hi_b
+                            mma_f16(d, ahd, sdesc_kmajor_sw64(bl + kk * 32), idesc16, 1u);     // hi_a * lo_b
+                            mma_f16(d, ahd, bhd, idesc16, 1u);                                 // hi_a * hi_b
+                        }
+                        mma_commit(empty_bar(stage));
+                        if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                        continue;
+                    }
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t ad = sdesc_kmajor_sw128(sa + kk * 32);
@@ -196,7 +241,9 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             const int row = tm * kBM + q * 32 + lane;
             const bool row_ok = row < G.M;
             float* crow = G.C + (long long)b * G.c_batch_stride + (long long)(row_ok ? row : 0) * G.ldc;
-            const float alpha = G.alpha, beta = G.beta;
+            float alpha = G.alpha;
+            const float beta = G.beta;
+            if (Cfg::k16 && G.scale) alpha = alpha / (G.scale[0] * G.scale[1]);  // undo the operand scaling
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 uint32_t r[32];
@@ -236,6 +283,48 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             mbar_arrive(tempty_bar(acc));
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
+        }
+    } else if (Cfg::k16 && warp >= 8) {
+        // ------------------------------------------------ fp32 -> 16-bit hi/lo
+        // Reads the 128-byte-swizzled fp32 stage and writes hi = rn16(s*x),
+        // lo = rn16(s*x - hi) into 64-byte-swizzled K-major tiles (16-byte chunk
+        // j of row r sits at chunk j ^ ((r >> 1) & 3)); s is the group's
+        // power-of-two operand scale (1 without one).
+        const int tid = threadIdx.x - 256;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            int g, b, tm, tn;
+            decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+            const GemmGroup& G = groups[g];
+            const int nk = (G.K + kBK - 1) / kBK;
+            const float s_a = G.scale ? G.scale[0] : 1.0f;
+            const float s_b = G.scale ? G.scale[1] : 1.0f;
+            for (int kb = 0; kb < nk; ++kb) {
+                bool w = mbar_wait(full_bar(stage), phase, abort_flag, status);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                const float4* src = reinterpret_cast<const float4*>(base_ptr + stage * Cfg::kStageBytes);
+                uint8_t* cv = base_ptr + (lo0 - base) + stage * Cfg::kStageBytes;
+#pragma unroll 4
+                for (int i = tid; i < Cfg::kStageBytes / 16; i += 128) {
+                    const bool is_a = i < kBM * 8;
+                    const int r = is_a ? (i >> 3) : ((i - kBM * 8) >> 3);
+                    const int c = (i & 7) ^ (r & 7);                    // logical 16-byte chunk of the fp32 row
+                    const float sc = is_a ? s_a : s_b;
+                    const float4 v = src[i];
+                    uint2 hi, lo;
+                    split16<MODE == kLeafBF16x3>(v.x * sc, v.y * sc, v.z * sc, v.w * sc, hi, lo);
+                    const int off = r * 64 + ((((c >> 1) ^ ((r >> 1) & 3))) << 4) + ((c & 1) << 3);
+                    uint8_t* hbase = cv + (is_a ? 0 : kBM * 64);
+                    uint8_t* lbase = cv + kBM * 64 + BN * 64 + (is_a ? 0 : kBM * 64);
+                    *reinterpret_cast<uint2*>(hbase + off) = hi;
+                    *reinterpret_cast<uint2*>(lbase + off) = lo;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(ready_bar(stage));
+                if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+            }
         }
     } else if (MODE == kLeaf3xTF32 && warp >= 8) {
         // ------------------------------------------------ hi/lo split
@@ -303,12 +392,16 @@ size_t leaf_smem_bytes(int mode, int bn) {
 }
 
 cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms, cudaStream_t stream) {
-    if (mode == kLeafTF32) {
-        return bn == 256 ? launch_impl<256, kLeafTF32>(args, num_sms, stream)
-                         : launch_impl<128, kLeafTF32>(args, num_sms, stream);
+#define FMM_LEAF(MODE_)                                                                 \
+    return bn == 256 ? launch_impl<256, MODE_>(args, num_sms, stream)                  \
+                     : launch_impl<128, MODE_>(args, num_sms, stream)
+    switch (mode) {
+        case kLeafTF32: FMM_LEAF(kLeafTF32);
+        case kLeafBF16x3: FMM_LEAF(kLeafBF16x3);
+        case kLeafFP16x3: FMM_LEAF(kLeafFP16x3);
+        default: FMM_LEAF(kLeaf3xTF32);
     }
-    return bn == 256 ? launch_impl<256, kLeaf3xTF32>(args, num_sms, stream)
-                     : launch_impl<128, kLeaf3xTF32>(args, num_sms, stream);
+#undef FMM_LEAF
 }
 
 }  // namespace fmm

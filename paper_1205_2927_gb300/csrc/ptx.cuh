@@ -140,6 +140,16 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
            | (static_cast<uint64_t>(2) << 61);               // swizzle mode: 128 B
 }
 
+// Same for a 16-bit operand tile with 64-byte rows (32 elements of K) and
+// 64-byte swizzle: 8-row / 512-byte atoms.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
+    return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4)
+           | (static_cast<uint64_t>(1) << 16)
+           | (static_cast<uint64_t>(512 >> 4) << 32)         // stride byte offset: 8 rows x 64 B
+           | (static_cast<uint64_t>(1) << 46)
+           | (static_cast<uint64_t>(4) << 61);               // swizzle mode: 64 B
+}
+
 // Instruction descriptor, dense, D = f32, both operands K-major.
 // a/b format: kind::f16 -> 0 = f16, 1 = bf16; kind::tf32 -> 2 = tf32.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, int M, int N) {

@@ -283,3 +283,81 @@ class BatchedPlan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ planner / cost model
+
+NPARAM = 4673
+
+
+def _planner_argtypes():
+    vp, i64, sz = C.c_void_p, C.c_int64, C.c_size_t
+    ip, fp = C.POINTER(C.c_int), C.POINTER(C.c_float)
+    _lib.fmm_autotune.argtypes = [i64, i64, i64, C.POINTER(Options), vp, vp, vp, vp, sz, C.POINTER(sz), ip, ip, fp,
+                                  ip, C.c_int, vp]
+    _lib.fmm_autotune.restype = C.c_int
+    _lib.fmm_plan_features.argtypes = [i64, i64, i64, C.c_int, C.c_int, C.c_int, fp]
+    _lib.fmm_plan_features.restype = C.c_int
+    _lib.fmm_mlp_forward.argtypes = [vp, vp, vp, C.c_int, vp]
+    _lib.fmm_mlp_forward.restype = C.c_int
+    _lib.fmm_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, vp, vp, C.c_int, vp, sz, C.POINTER(sz), vp,
+                                        vp, vp]
+    _lib.fmm_mlp_train_step.restype = C.c_int
+    _lib.fmm_set_cost_model.argtypes = [fp, fp, fp]
+    _lib.fmm_set_cost_model.restype = C.c_int
+
+
+_planner_argtypes()
+
+
+def fmm_autotune(M, N, K, A, B, Cmat, reps=1, stream=None, **opt_kwargs):
+    """Time every candidate plan on device tensors A, B, C (C is overwritten).
+    Returns a list of (depth, leaf_tile, milliseconds)."""
+    import torch
+    opt = options(**opt_kwargs)
+    need = C.c_size_t(0)
+    n = C.c_int(0)
+    _check(_lib.fmm_autotune(M, N, K, C.byref(opt), None, None, None, None, 0, C.byref(need), None, None, None,
+                             C.byref(n), reps, None), "fmm_autotune(query)")
+    ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=A.device)
+    d, t, ms = (C.c_int * 16)(), (C.c_int * 16)(), (C.c_float * 16)()
+    _check(_lib.fmm_autotune(M, N, K, C.byref(opt), A.data_ptr(), B.data_ptr(), Cmat.data_ptr(), ws.data_ptr(),
+                             ws.numel(), C.byref(need), d, t, ms, C.byref(n), reps, _stream_ptr(stream)),
+           "fmm_autotune")
+    return [(d[i], t[i], ms[i]) for i in range(n.value)]
+
+
+def fmm_plan_features(M, N, K, depth, leaf_tile, precision=0):
+    out = (C.c_float * 6)()
+    _check(_lib.fmm_plan_features(M, N, K, depth, leaf_tile, precision, out), "fmm_plan_features")
+    return list(out)
+
+
+def fmm_mlp_forward(params, X, Y, stream=None):
+    _check(_lib.fmm_mlp_forward(params.data_ptr(), X.data_ptr(), Y.data_ptr(), X.shape[0], _stream_ptr(stream)),
+           "fmm_mlp_forward")
+
+
+def fmm_mlp_train_step(params, m, v, step, lr, X, T, workspace, grad_out=None, loss_out=None, stream=None):
+    _check(_lib.fmm_mlp_train_step(params.data_ptr(), m.data_ptr(), v.data_ptr(), step, lr, X.data_ptr(),
+                                   T.data_ptr(), X.shape[0], workspace.data_ptr(), workspace.numel(), None,
+                                   grad_out.data_ptr() if grad_out is not None else None,
+                                   loss_out.data_ptr() if loss_out is not None else None, _stream_ptr(stream)),
+           "fmm_mlp_train_step")
+
+
+def mlp_workspace_bytes(batch):
+    need = C.c_size_t(0)
+    _check(_lib.fmm_mlp_train_step(None, None, None, 1, 0.0, None, None, batch, None, 0, C.byref(need), None, None,
+                                   None), "fmm_mlp_train_step(query)")
+    return need.value
+
+
+def fmm_set_cost_model(params=None, mean=None, std=None):
+    if params is None:
+        _check(_lib.fmm_set_cost_model(None, None, None), "fmm_set_cost_model")
+        return
+    P = (C.c_float * NPARAM)(*[float(x) for x in params])
+    Mn = (C.c_float * 6)(*[float(x) for x in mean])
+    Sd = (C.c_float * 6)(*[float(x) for x in std])
+    _check(_lib.fmm_set_cost_model(P, Mn, Sd), "fmm_set_cost_model")

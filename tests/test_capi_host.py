@@ -111,3 +111,30 @@ def test_peel_workspace_has_no_padding(F):
     s_core = _query(F, 992, 992, 992, depth=3, odd="pad")
     assert s_peel > s_core        # core buffers + transposed B and aligned A for the border
     assert s_pad > s_core         # 1000 -> 1024
+
+
+def test_plan_features_and_cost_model_file(F, tmp_path):
+    import numpy as np
+    from paper_1205_2927_gb300 import planner as PL
+    assert F.fmm_plan_features(4096, 2048, 1024, 2, 256, 1) == [12.0, 10.0, 11.0, 2.0, 2.0, 1.0]
+    p = PL.init_params(3)
+    assert p.shape == (F.NPARAM,)
+    PL.save(tmp_path / "m.bin", p, np.arange(6), np.ones(6))
+    q, mean, std = PL.load(tmp_path / "m.bin")
+    assert np.array_equal(q, p) and np.array_equal(mean, np.arange(6)) and np.all(std == 1)
+
+
+def test_cost_model_registration_validates(F):
+    import ctypes
+    lib = F.library()
+    P = (ctypes.c_float * F.NPARAM)()
+    m = (ctypes.c_float * 6)()
+    bad = (ctypes.c_float * 6)(*([1.0] * 5 + [0.0]))
+    assert lib.fmm_set_cost_model(P, m, bad) == 1
+    assert lib.fmm_set_cost_model(None, None, None) == 0
+
+
+def test_exhaustive_query_includes_scratch(F):
+    fixed = _query(F, 2048, 2048, 2048, planner="fixed", depth=1)
+    ex = _query(F, 2048, 2048, 2048, planner="exhaustive")
+    assert ex > fixed + 3 * 2048 * 2048 * 4 - 1

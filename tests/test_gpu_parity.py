@@ -222,3 +222,55 @@ def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64):
     want = O.freivalds(A, B, Cx, x)
     assert np.array_equal(got, want)           # integer data: exact in both accumulations
     assert np.count_nonzero(got) == 1 and abs(got[123]) == 1.0
+
+
+# --- split-precision leaves (BF16x3, FP16x3) ----------------------------------
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("m,k,n,d", [(256, 96, 384, 0), (300, 200, 260, 0), (512, 512, 512, 2), (300, 200, 260, 1)])
+def test_split16_bit_exact_small_int(fmm, prec, m, k, n, d):
+    A = I.small_int((m, k), 8000 + m + d, r=2)
+    B = I.small_int((k, n), 8100 + n + d, r=2)
+    C, _ = run(fmm, A, B, depth=d, precision=prec)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(C, ref)
+
+
+def _fp16_scale(x, bound=1.0):
+    # largest power of two s with bound * max|x| * s <= 2^14
+    m = float(np.max(np.abs(x))) * bound
+    e = 14 - (np.frexp(m)[1])
+    return 2.0 ** e
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_split16_matches_three_product_model(fmm, prec):
+    m, k, n = 256, 512, 256
+    A, B = I.operands(m, k, n, 78, "normal")
+    C, _ = run(fmm, A, B, depth=0, precision=prec)
+    if prec == "bf16x3":
+        Ah, Al = O.split_bf16(A)
+        Bh, Bl = O.split_bf16(B)
+        model = O.split_product(Ah, Al, Bh, Bl)
+    else:
+        sa, sb = _fp16_scale(A), _fp16_scale(B)
+        Ah, Al = O.split_fp16(A, sa)
+        Bh, Bl = O.split_fp16(B, sb)
+        model = O.split_product(Ah, Al, Bh, Bl) / (sa * sb)
+    scale = np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64)
+    assert np.max(np.abs(C - model) / scale) <= 4 * k * 2.0 ** -24
+    # and the split model itself is within its own error of the exact product
+    err = O.error_metric(C, O.classical(A, B), A, B)
+    assert err <= (2e-5 if prec == "bf16x3" else 2e-6)
+
+
+@pytest.mark.parametrize("prec,dist,d", [("bf16x3", "normal", 2), ("fp16x3", "loguniform", 3),
+                                         ("fp16x3", "loguniform", 4), ("tf32", "normal", 1)])
+def test_split_precision_winograd_bounds(fmm, prec, dist, d):
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(3, d), dist)
+    C, _ = run(fmm, A, B, depth=d, precision=prec)
+    assert np.all(np.isfinite(C))
+    err = O.error_metric(C, O.classical(A, B), A, B)
+    bound = {"bf16x3": 5e-5, "fp16x3": 2e-6, "tf32": 5e-5}[prec]
+    assert err <= bound, err

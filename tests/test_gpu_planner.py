@@ -1,0 +1,112 @@
+"""GPU tests of the planner: the cost-model kernels against the float64 CPU
+oracle (forward, gradients, Adam), the exhaustive autotuner, and an end-to-end
+learned-planner run compared with the fixed-threshold planner."""
+import numpy as np
+import pytest
+
+import oracle.fmm_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1205_2927_gb300 import fmm
+    return fmm
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, 6)).astype(np.float32)
+    t = (0.5 * X[:, 0] - X[:, 3] * X[:, 1] + 0.2).astype(np.float32)
+    theta = (rng.standard_normal(O.MLP_NPARAM) * 0.3).astype(np.float32)
+    return X, t, theta
+
+
+def test_mlp_forward_matches_oracle(F):
+    import torch
+    X, _, theta = _data(300, 1)
+    Y = torch.empty(300, device="cuda")
+    F.fmm_mlp_forward(torch.from_numpy(theta).cuda(), torch.from_numpy(X).cuda(), Y)
+    ref, _ = O.mlp_forward(theta.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(Y.cpu().numpy(), ref, rtol=1e-4, atol=1e-4)
+
+
+def test_mlp_gradients_match_oracle(F):
+    import torch
+    X, t, theta = _data(257, 2)
+    p = torch.from_numpy(theta).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    g = torch.empty_like(p)
+    loss = torch.zeros(1, device="cuda")
+    ws = torch.empty(F.mlp_workspace_bytes(257), dtype=torch.uint8, device="cuda")
+    F.fmm_mlp_train_step(p, m, v, 1, 0.0, torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda(), ws,
+                         grad_out=g, loss_out=loss)
+    lref, gref = O.mlp_grad(theta.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(lref, rel=1e-4)
+    gg = g.cpu().numpy()
+    scale = np.abs(gref).max()
+    assert np.max(np.abs(gg - gref)) <= 1e-4 * scale + 1e-7
+    assert np.array_equal(p.cpu().numpy(), theta)  # lr = 0: no update
+
+
+def test_adam_step_matches_oracle_and_training_converges(F):
+    import torch
+    X, t, theta = _data(512, 3)
+    dX, dT = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    p = torch.from_numpy(theta).cuda()
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    ws = torch.empty(F.mlp_workspace_bytes(512), dtype=torch.uint8, device="cuda")
+    F.fmm_mlp_train_step(p, m, v, 1, 1e-3, dX, dT, ws)
+    _, g64 = O.mlp_grad(theta.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    ref, _, _ = O.adam_step(theta.astype(np.float64), np.zeros(O.MLP_NPARAM), np.zeros(O.MLP_NPARAM), g64, 1, 1e-3)
+    # first Adam step moves each parameter by ~lr * sign(g): compare the moves
+    mv = p.cpu().numpy() - theta
+    mvref = ref - theta
+    big = np.abs(g64) > 1e-3 * np.abs(g64).max()
+    assert np.allclose(mv[big], mvref[big], rtol=1e-3, atol=1e-6)
+    loss = torch.zeros(1, device="cuda")
+    l0 = O.mlp_loss(theta.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
+    for s in range(2, 400):
+        F.fmm_mlp_train_step(p, m, v, s, 3e-3, dX, dT, ws, loss_out=loss)
+    assert float(loss.item()) < 0.2 * l0
+
+
+def test_autotune_and_exhaustive_planner(F):
+    import torch
+    M, K, N = 1536, 1024, 2048
+    A = torch.rand(M, K, device="cuda") * 2 - 1
+    B = torch.rand(K, N, device="cuda") * 2 - 1
+    C = torch.empty(M, N, device="cuda")
+    res = F.fmm_autotune(M, N, K, A, B, C, reps=2)
+    depths = sorted(set(d for d, _, _ in res))
+    assert depths[0] == 0 and len(depths) >= 3 and all(ms > 0 for _, _, ms in res)
+    p = F.Plan(M, N, K, planner="exhaustive")
+    assert (p.info["depth"], p.info["leaf_tile"]) in [(d, t) for d, t, _ in res]
+    out = p(A, B)
+    torch.cuda.synchronize()
+    ref = O.classical(A.cpu().numpy(), B.cpu().numpy())
+    assert O.error_metric(out.cpu().numpy(), ref, A.cpu().numpy(), B.cpu().numpy()) <= 2e-6
+    p.close()
+
+
+def test_learned_planner_end_to_end(F):
+    from paper_1205_2927_gb300 import inputs as I
+    from paper_1205_2927_gb300 import planner as PL
+    train_shapes = I.batched_shapes(90, 7100, lo=256, hi=4096, multiple=4)
+    test_shapes = I.batched_shapes(25, 7200, lo=256, hi=4096, multiple=4)
+    recs = PL.collect(train_shapes, reps=1, seed=1)
+    X, y = PL.features(recs)
+    params, mean, std, losses = PL.train(X, y, steps=800, lr=3e-3)
+    assert losses[-1][1] < 0.1 * float(np.var(y))
+    PL.register(params, mean, std)
+    try:
+        ev = PL.evaluate(PL.collect(test_shapes, reps=1, seed=2))
+    finally:
+        F.fmm_set_cost_model(None)
+    s = PL.summary(ev)
+    print(s)
+    assert s["regret_mlp"] <= 0.25
+    assert s["total_ms_mlp"] <= 1.05 * s["total_ms_fixed"]
