@@ -311,6 +311,65 @@ __global__ void fp16_scale_kernel(const unsigned* mx, float bound_mult, float* s
     scale[i] = ldexpf(1.0f, e);
 }
 
+// Root pre-additions of the host-streamed schedule: the four quadrants are
+// separate row-major buffers (h x w, row stride ld); writes the four sums.
+//   A side: S1 = Q2 + Q3, S2 = S1 - Q0, S3 = Q0 - Q2, S4 = Q1 - S2
+//   B side: T1 = Q1 - Q0, T2 = Q3 - T1, T3 = Q3 - Q1, T4 = T2 - Q2
+template <int SIDE_B>
+__global__ void __launch_bounds__(128) quad_pre_kernel(QuadPre q) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= q.w) return;
+    for (long long r = blockIdx.y; r < q.h; r += gridDim.y) {
+        const long long o = r * q.ld + c;
+        const float4 Q0 = *reinterpret_cast<const float4*>(q.in[0] + o);
+        const float4 Q1 = *reinterpret_cast<const float4*>(q.in[1] + o);
+        const float4 Q2 = *reinterpret_cast<const float4*>(q.in[2] + o);
+        const float4 Q3 = *reinterpret_cast<const float4*>(q.in[3] + o);
+        float4 X1, X2, X3, X4;
+        if (!SIDE_B) {
+            X1 = add4(Q2, Q3); X2 = sub4(X1, Q0); X3 = sub4(Q0, Q2); X4 = sub4(Q1, X2);
+        } else {
+            X1 = sub4(Q1, Q0); X2 = sub4(Q3, X1); X3 = sub4(Q3, Q1); X4 = sub4(X2, Q2);
+        }
+        *reinterpret_cast<float4*>(q.out[0] + o) = X1;
+        *reinterpret_cast<float4*>(q.out[1] + o) = X2;
+        *reinterpret_cast<float4*>(q.out[2] + o) = X3;
+        *reinterpret_cast<float4*>(q.out[3] + o) = X4;
+    }
+}
+
+// Root post-additions of the host-streamed schedule from the seven product
+// buffers (h x w, row stride ld) into quadrant buffers of C (same layout):
+//   part 0: C11 = alpha * (P1 + P2) + beta * C11
+//   part 1: C12 = alpha * U5, C21 = alpha * U6, C22 = alpha * U7 (+ beta * old)
+template <int PART>
+__global__ void __launch_bounds__(128) quad_post_kernel(QuadPost q) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= q.w) return;
+    for (long long r = blockIdx.y; r < q.h; r += gridDim.y) {
+        const long long o = r * q.ld + c;
+        auto P = [&](int i) { return *reinterpret_cast<const float4*>(q.p[i] + o); };
+        auto put = [&](float* dst, float4 u) {
+            float4 v = f4(q.alpha * u.x, q.alpha * u.y, q.alpha * u.z, q.alpha * u.w);
+            if (q.beta != 0.0f) {
+                const float4 old = *reinterpret_cast<const float4*>(dst + o);
+                v.x += q.beta * old.x; v.y += q.beta * old.y; v.z += q.beta * old.z; v.w += q.beta * old.w;
+            }
+            *reinterpret_cast<float4*>(dst + o) = v;
+        };
+        if (PART == 0) {
+            put(q.c[0], add4(P(0), P(1)));
+        } else {
+            const float4 U2 = add4(P(0), P(5));
+            const float4 U3 = add4(U2, P(6));
+            const float4 U4 = add4(U2, P(4));
+            put(q.c[1], add4(U4, P(2)));   // U5 = U4 + P3
+            put(q.c[2], sub4(U3, P(3)));   // U6 = U3 - P4
+            put(q.c[3], add4(U3, P(4)));   // U7 = U3 + P5
+        }
+    }
+}
+
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -393,6 +452,22 @@ cudaError_t launch_fp16_scales(const float* A, long long lda, long long M, long 
     if (M > 0 && K > 0) absmax_kernel<<<dim3(4, gy(M < 1024 ? M : 1024)), 256, 0, stream>>>(A, lda, M, K, scratch);
     if (K > 0 && N > 0) absmax_kernel<<<dim3(4, gy(K < 1024 ? K : 1024)), 256, 0, stream>>>(B, ldb, K, N, scratch + 1);
     fp16_scale_kernel<<<1, 32, 0, stream>>>(scratch, bound_mult, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quad_pre(const QuadPre& q, int side_b, cudaStream_t stream) {
+    if (q.h <= 0 || q.w <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((q.w + 511) / 512), gy(q.h));
+    if (side_b) quad_pre_kernel<1><<<grid, 128, 0, stream>>>(q);
+    else quad_pre_kernel<0><<<grid, 128, 0, stream>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quad_post(const QuadPost& q, int part, cudaStream_t stream) {
+    if (q.h <= 0 || q.w <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((q.w + 511) / 512), gy(q.h));
+    if (part == 0) quad_post_kernel<0><<<grid, 128, 0, stream>>>(q);
+    else quad_post_kernel<1><<<grid, 128, 0, stream>>>(q);
     return cudaGetLastError();
 }
 

@@ -139,6 +139,16 @@ struct fmm_plan_s {
     long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
     int peel = 0;
     float border_beta = 0.f;
+    // host-resident operands: root level depth-first over the 7 products with
+    // quadrant transfers on two copy streams; children run on device buffers
+    int host = 0;
+    fmm_plan_s* child = nullptr;
+    float* hq[27] = {};               // A quads 0-3, B quads 4-7, S 8-11, T 12-15, P 16-22, C quads 23-26
+    long long hm = 0, hk = 0, hn = 0; // quadrant sizes
+    char* child_ws = nullptr;
+    size_t child_ws_bytes = 0;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t hev[6] = {};
     // FP16x3: device operand scales {s_a, s_b} and reduction scratch, inside the status block
     float* fp16_scale() const { return reinterpret_cast<float*>(status + 16); }
     unsigned* fp16_scratch() const { return status + 24; }
@@ -177,10 +187,38 @@ struct Carver {
     }
 };
 
+void make_child(const fmm_plan_s* p, fmm_plan_s& c);
+
 void layout(fmm_plan_s* p, char* ws, size_t* needed) {
     Carver cv(ws);
     p->status = cv.take<unsigned>(64);
     const int d = p->depth;
+    if (p->host) {
+        // device copies of the root quadrants; the children run on these
+        const long long g = d > 0 ? (4LL << d) : 4;
+        p->M0 = rup(p->M, g); p->K0 = rup(p->K, g); p->N0 = rup(p->N, g);
+        p->Mw = p->M; p->Kw = p->K; p->Nw = p->N;
+        const int parts = d > 0 ? 2 : 1;   // depth 0: one "quadrant" = the whole matrix
+        p->hm = p->M0 / parts; p->hk = p->K0 / parts; p->hn = p->N0 / parts;
+        const size_t qa = (size_t)(p->hm * p->hk), qb = (size_t)(p->hk * p->hn), qc = (size_t)(p->hm * p->hn);
+        const int nq = d > 0 ? 4 : 1;
+        for (int i = 0; i < nq; ++i) p->hq[i] = cv.take<float>(qa);
+        for (int i = 0; i < nq; ++i) p->hq[4 + i] = cv.take<float>(qb);
+        for (int i = 0; i < nq; ++i) p->hq[23 + i] = cv.take<float>(qc);
+        if (d > 0) {
+            for (int i = 0; i < 4; ++i) p->hq[8 + i] = cv.take<float>(qa);
+            for (int i = 0; i < 4; ++i) p->hq[12 + i] = cv.take<float>(qb);
+            for (int i = 0; i < 7; ++i) p->hq[16 + i] = cv.take<float>(qc);
+        }
+        fmm_plan_s c;
+        make_child(p, c);
+        size_t cneed = 0;
+        layout(&c, nullptr, &cneed);
+        p->child_ws_bytes = cneed;
+        p->child_ws = cv.take<char>(cneed);
+        if (needed) *needed = align_up(cv.off, 256);
+        return;
+    }
     if (d == 0) {
         p->ld_bt = rup(p->K, 4);
         p->Bt = cv.take<float>((size_t)p->N * p->ld_bt);
@@ -261,7 +299,8 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL) return FMM_ERR_INVALID_ARG;
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
-    if (o->algo == FMM_ALGO_CLASSICAL || o->host_operands) return FMM_ERR_UNSUPPORTED;
+    if (o->algo == FMM_ALGO_CLASSICAL) return FMM_ERR_UNSUPPORTED;
+    if (o->host_operands && o->odd != FMM_ODD_PAD) return FMM_ERR_UNSUPPORTED;
     return FMM_OK;
 }
 
@@ -698,6 +737,7 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
               const fmm_options_t& o, int depth, int bn) {
     t.M = M; t.N = N; t.K = K; t.lda = lda; t.ldb = ldb; t.ldc = ldc;
     t.opt = o;
+    t.host = o.host_operands ? 1 : 0;
     t.depth = (M == 0 || N == 0 || K == 0) ? 0 : depth;
     t.peel = (o.odd == FMM_ODD_PEEL) ? 1 : 0;
     if (t.peel && t.depth > 0) {
@@ -754,6 +794,116 @@ void raw_features(long long M, long long N, long long K, int depth, int bn, int 
     f[5] = (float)prec;
 }
 
+// Child problem of a host-resident plan: one root quadrant product on device
+// buffers (depth - 1 levels), or the whole product at depth 0.
+void make_child(const fmm_plan_s* p, fmm_plan_s& c) {
+    fmm_options_t o = p->opt;
+    o.host_operands = 0;
+    make_tmp(c, p->hm, p->hn, p->hk, p->hk, p->hn, p->hn, o, p->depth > 0 ? p->depth - 1 : 0, p->bn);
+}
+
+// Host-resident multiply.  The root level runs depth-first over the seven
+// products so that transfers overlap compute: A11, B11 are copied first (P1
+// starts on them), then A12, B21 (P2), then the rest; C11 = P1 + P2 is copied
+// back while P3..P7 run.  Copies run on the plan's two copy streams, ordered
+// after `stream` by events; `stream` waits for the last device-to-host copy.
+fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
+                      cudaStream_t stream) {
+    for (const void* ptr : {(const void*)A, (const void*)B, (const void*)C}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return FMM_ERR_INVALID_ARG;
+        }
+        if (at.type == cudaMemoryTypeUnregistered) {
+            snprintf(g_last_error, sizeof(g_last_error), "host operands must be page-locked (pinned) memory");
+            return FMM_ERR_INVALID_ARG;
+        }
+    }
+    fmm_plan_s* c = p->child;
+    cudaEvent_t* ev = p->hev;
+    float** q = p->hq;
+    const long long hm = p->hm, hk = p->hk, hn = p->hn;
+    FMM_CUDA(cudaEventRecord(ev[0], stream));
+    FMM_CUDA(cudaStreamWaitEvent(p->s_h2d, ev[0], 0));
+    FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[0], 0));
+    // valid part of quadrant (qi, qj) of an R x W host matrix split at (h, w)
+    auto copy = [&](bool to_dev, float* dev, long long ldd, const float* host_c, float* host, long long ldh,
+                    long long R, long long W, long long h, long long w, int qi, int qj) -> fmm_status_t {
+        const long long r0 = qi * h, c0 = qj * w;
+        const long long rows = std::min(h, R - r0), cols = std::min(w, W - c0);
+        if (rows <= 0 || cols <= 0) return FMM_OK;
+        if (to_dev)
+            FMM_CUDA(cudaMemcpy2DAsync(dev, ldd * 4, host_c + r0 * ldh + c0, ldh * 4, cols * 4, rows,
+                                       cudaMemcpyHostToDevice, p->s_h2d));
+        else
+            FMM_CUDA(cudaMemcpy2DAsync(host + r0 * ldh + c0, ldh * 4, dev, ldd * 4, cols * 4, rows,
+                                       cudaMemcpyDeviceToHost, p->s_d2h));
+        return FMM_OK;
+    };
+    auto inA = [&](int i) { return copy(true, q[i], hk, A, nullptr, p->lda, p->M, p->K, hm, hk, i / 2, i % 2); };
+    auto inB = [&](int i) { return copy(true, q[4 + i], hn, B, nullptr, p->ldb, p->K, p->N, hk, hn, i / 2, i % 2); };
+    auto inC = [&](int i) { return copy(true, q[23 + i], hn, C, nullptr, p->ldc, p->M, p->N, hm, hn, i / 2, i % 2); };
+    auto outC = [&](int i) { return copy(false, q[23 + i], hn, nullptr, C, p->ldc, p->M, p->N, hm, hn, i / 2, i % 2); };
+    fmm_status_t s;
+#define FMM_TRY(x) do { if ((s = (x)) != FMM_OK) return s; } while (0)
+    if (p->depth == 0) {
+        FMM_TRY(inA(0));
+        FMM_TRY(inB(0));
+        if (beta != 0.0f) FMM_TRY(inC(0));
+        FMM_CUDA(cudaEventRecord(ev[1], p->s_h2d));
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[1], 0));
+        FMM_TRY(execute(c, alpha, q[0], q[4], beta, q[23], stream));
+        FMM_CUDA(cudaEventRecord(ev[4], stream));
+        FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[4], 0));
+        FMM_TRY(outC(0));
+    } else {
+        // transfers in order of first use
+        FMM_TRY(inA(0)); FMM_TRY(inB(0));                        // A11, B11 -> P1
+        if (beta != 0.0f) for (int i = 0; i < 4; ++i) FMM_TRY(inC(i));
+        FMM_CUDA(cudaEventRecord(ev[1], p->s_h2d));
+        FMM_TRY(inA(1)); FMM_TRY(inB(2));                        // A12, B21 -> P2
+        FMM_CUDA(cudaEventRecord(ev[2], p->s_h2d));
+        FMM_TRY(inA(2)); FMM_TRY(inA(3)); FMM_TRY(inB(1)); FMM_TRY(inB(3));
+        FMM_CUDA(cudaEventRecord(ev[3], p->s_h2d));
+        float* P[7];
+        for (int i = 0; i < 7; ++i) P[i] = q[16 + i];
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[1], 0));
+        FMM_TRY(execute(c, 1.f, q[0], q[4], 0.f, P[0], stream));   // P1 = A11 B11
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[2], 0));
+        FMM_TRY(execute(c, 1.f, q[1], q[6], 0.f, P[1], stream));   // P2 = A12 B21
+        QuadPost qp{};
+        for (int i = 0; i < 7; ++i) qp.p[i] = P[i];
+        for (int i = 0; i < 4; ++i) qp.c[i] = q[23 + i];
+        qp.ld = hn; qp.h = hm; qp.w = hn; qp.alpha = alpha; qp.beta = beta;
+        FMM_CUDA(launch_quad_post(qp, 0, stream));                // C11 = alpha U1 + beta C11
+        FMM_CUDA(cudaEventRecord(ev[4], stream));
+        FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[4], 0));
+        FMM_TRY(outC(0));
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[3], 0));
+        QuadPre pa{{q[0], q[1], q[2], q[3]}, {q[8], q[9], q[10], q[11]}, hk, hm, hk};
+        QuadPre pb{{q[4], q[5], q[6], q[7]}, {q[12], q[13], q[14], q[15]}, hn, hk, hn};
+        FMM_CUDA(launch_quad_pre(pa, 0, stream));                 // S1..S4
+        FMM_CUDA(launch_quad_pre(pb, 1, stream));                 // T1..T4
+        FMM_TRY(execute(c, 1.f, q[11], q[7], 0.f, P[2], stream));  // P3 = S4 B22
+        FMM_TRY(execute(c, 1.f, q[3], q[15], 0.f, P[3], stream));  // P4 = A22 T4
+        FMM_TRY(execute(c, 1.f, q[8], q[12], 0.f, P[4], stream));  // P5 = S1 T1
+        FMM_TRY(execute(c, 1.f, q[9], q[13], 0.f, P[5], stream));  // P6 = S2 T2
+        FMM_TRY(execute(c, 1.f, q[10], q[14], 0.f, P[6], stream)); // P7 = S3 T3
+        FMM_CUDA(launch_quad_post(qp, 1, stream));                // C12, C21, C22
+        FMM_CUDA(cudaEventRecord(ev[5], stream));
+        FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[5], 0));
+        FMM_TRY(outC(1)); FMM_TRY(outC(2)); FMM_TRY(outC(3));
+        p->launches += 4;
+    }
+#undef FMM_TRY
+    FMM_CUDA(cudaEventRecord(ev[0], p->s_d2h));
+    FMM_CUDA(cudaStreamWaitEvent(stream, ev[0], 0));
+    p->launches += c->launches;
+    c->launches = 0;
+    return FMM_OK;
+}
+
 // Score the candidates with the registered network (one inference launch) and
 // return the index of the smallest predicted time (ties: smaller depth, then
 // the larger tile).
@@ -806,7 +956,9 @@ fmm_status_t autotune_core(long long M, long long N, long long K, const fmm_opti
     s = FMM_OK;
     for (int i = 0; i < n && s == FMM_OK; ++i) {
         fmm_plan_s t;
-        make_tmp(t, M, N, K, K, N, N, o, c[i].depth, c[i].bn);
+        fmm_options_t od = o;
+        od.host_operands = 0;   // candidates are timed on device operands
+        make_tmp(t, M, N, K, K, N, N, od, c[i].depth, c[i].bn);
         size_t need = 0;
         layout(&t, nullptr, &need);
         if (need > ws_bytes) { s = FMM_ERR_WORKSPACE; break; }
@@ -861,9 +1013,11 @@ fmm_status_t plan_choose(long long M, long long N, long long K, long long lda, l
     // exhaustive (also the fallback of the learned planner): the largest
     // candidate plus scratch operands for the timing runs
     size_t mx = 0;
+    fmm_options_t od = o;
+    od.host_operands = 0;
     for (int i = 0; i < n; ++i) {
         fmm_plan_s t;
-        make_tmp(t, M, N, K, K, N, N, o, c[i].depth, c[i].bn);
+        make_tmp(t, M, N, K, K, N, N, od, c[i].depth, c[i].bn);
         size_t q = 0;
         layout(&t, nullptr, &q);
         mx = std::max(mx, q);
@@ -1105,6 +1259,29 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
     layout(p, p->ws, nullptr);
     cudaError_t e = cudaMemsetAsync(p->status, 0, 64 * sizeof(unsigned), (cudaStream_t)stream);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMemsetAsync(status)"); }
+    if (p->host) {
+        fmm_plan_s c;
+        make_child(p, c);
+        p->child = new (std::nothrow) fmm_plan_s(c);
+        if (!p->child) { fmm_free(p); return FMM_ERR_OOM; }
+        layout(p->child, p->child_ws, nullptr);
+        p->child->ws = p->child_ws;
+        p->child->ws_bytes = p->child_ws_bytes;
+        p->child->num_sms = di.num_sms;
+        e = cudaMemsetAsync(p->child->status, 0, 64 * sizeof(unsigned), (cudaStream_t)stream);
+        // zero the quadrant buffers once: each call rewrites only the valid parts,
+        // so the padding rows/columns stay zero
+        const size_t qa = (size_t)(p->hm * p->hk), qb = (size_t)(p->hk * p->hn), qc = (size_t)(p->hm * p->hn);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+            if (p->hq[i]) e = cudaMemsetAsync(p->hq[i], 0, qa * 4, (cudaStream_t)stream);
+            if (e == cudaSuccess && p->hq[4 + i]) e = cudaMemsetAsync(p->hq[4 + i], 0, qb * 4, (cudaStream_t)stream);
+            if (e == cudaSuccess && p->hq[23 + i]) e = cudaMemsetAsync(p->hq[23 + i], 0, qc * 4, (cudaStream_t)stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) { fmm_free(p); return cuda_fail(e, "host-resident plan setup"); }
+    }
     p->last_stream = (cudaStream_t)stream;
     *out = p;
     return FMM_OK;
@@ -1133,7 +1310,7 @@ fmm_status_t fmm_gemm(fmm_plan_t p, float alpha, const float* A, const float* B,
         p->cur = &es;
         mark(p, 0, stream);
     }
-    fmm_status_t st = execute(p, alpha, A, B, beta, C, stream);
+    fmm_status_t st = p->host ? run_host(p, alpha, A, B, beta, C, stream) : execute(p, alpha, A, B, beta, C, stream);
     p->calls += 1;
     if (p->cur) {
         mark(p, 3, stream);
@@ -1183,6 +1360,13 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
 void fmm_free(fmm_plan_t p) {
     if (!p) return;
     drain_profile(p);
+    if (p->s_h2d) cudaStreamSynchronize(p->s_h2d);
+    if (p->s_d2h) cudaStreamSynchronize(p->s_d2h);
+    if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+    if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+    for (auto& e : p->hev)
+        if (e) cudaEventDestroy(e);
+    delete p->child;
     for (auto& es : p->ev_free)
         for (int i = 0; i < 4; ++i) cudaEventDestroy(es.e[i]);
     delete p;

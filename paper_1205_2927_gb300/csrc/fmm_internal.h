@@ -113,6 +113,21 @@ cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, long long total_
 cudaError_t launch_fp16_scales(const float* A, long long lda, long long M, long long K, const float* B,
                                long long ldb, long long N, float bound_mult, float* scale, unsigned* scratch,
                                cudaStream_t stream);
+// Host-streamed root level: quadrant buffers are separate (h x w, row stride
+// ld, all multiples of 4 floats, 16-byte aligned).
+struct QuadPre {
+    const float* in[4];   // Q0..Q3
+    float* out[4];        // the four sums, in order 1..4
+    long long ld, h, w;
+};
+struct QuadPost {
+    const float* p[7];    // P1..P7
+    float* c[4];          // C11, C12, C21, C22 quadrant buffers
+    long long ld, h, w;
+    float alpha, beta;
+};
+cudaError_t launch_quad_pre(const QuadPre& q, int side_b, cudaStream_t stream);
+cudaError_t launch_quad_post(const QuadPost& q, int part, cudaStream_t stream);
 // Deterministic pseudo-random fill of n floats in [-1, 1) (autotuner scratch).
 cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream);
 // Cost-model inference (mlp.cu): Y = f(X), `batch` rows of 6 features.

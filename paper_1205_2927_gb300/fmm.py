@@ -179,9 +179,12 @@ class Plan:
     def __call__(self, A, B, C=None, alpha=1.0, beta=0.0, stream=None):
         import torch
         if C is None:
-            C = torch.empty((self.M, self.ldc), dtype=torch.float32, device=A.device)[:, : self.N]
+            C = (torch.empty((self.M, self.ldc), dtype=torch.float32).pin_memory() if self.opt.host_operands
+                 else torch.empty((self.M, self.ldc), dtype=torch.float32, device=A.device))[:, : self.N]
         for t in (A, B, C):
-            assert t.dtype == torch.float32 and t.is_cuda
+            assert t.dtype == torch.float32
+            assert t.is_cuda or (self.opt.host_operands and t.is_pinned()), \
+                "operands must be CUDA tensors (or pinned host tensors with host_operands=1)"
         fmm_gemm(self.handle, alpha, A.data_ptr(), B.data_ptr(), beta, C.data_ptr(), stream)
         return C
 

@@ -1,0 +1,70 @@
+"""GPU parity of the host-resident path: operands in pinned host memory,
+quadrants streamed in order of first use, the root level depth-first."""
+import numpy as np
+import pytest
+
+import oracle.fmm_oracle as O
+from paper_1205_2927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1205_2927_gb300 import fmm
+    return fmm
+
+
+def run_host(F, A, B, C0=None, alpha=1.0, beta=0.0, **kw):
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = (torch.from_numpy(C0) if C0 is not None else torch.full((m, n), float("nan"))).pin_memory()
+    p = F.Plan(m, n, k, host_operands=1, **kw)
+    p(hA, hB, hC, alpha=alpha, beta=beta)
+    torch.cuda.current_stream().synchronize()
+    assert p.device_status() == 0
+    p.close()
+    return hC.numpy().copy()
+
+
+@pytest.mark.parametrize("m,k,n,d", [(300, 200, 260, 2), (512, 512, 512, 1), (777, 333, 515, 0),
+                                     (1024, 640, 768, 3), (130, 70, 90, 1)])
+def test_host_resident_bit_exact(F, m, k, n, d):
+    A = I.small_int((m, k), 11000 + m, r=2)
+    B = I.small_int((k, n), 11100 + n, r=2)
+    C = run_host(F, A, B, depth=d)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(C, ref)
+
+
+def test_host_resident_alpha_beta(F):
+    m, k, n = 290, 150, 330
+    A = I.small_int((m, k), 15, r=3)
+    B = I.small_int((k, n), 16, r=3)
+    C0 = I.small_int((m, n), 17, r=5)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
+    for d in (0, 2):
+        C = run_host(F, A, B, C0, alpha=2.0, beta=-1.0, depth=d)
+        assert np.array_equal(C, (2.0 * ref - C0).astype(np.float32))
+
+
+def test_host_resident_float_bound(F):
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(2, 9), "normal")
+    C = run_host(F, A, B, depth=2)
+    assert O.error_metric(C, O.classical(A, B), A, B) <= 2e-6
+
+
+def test_pageable_host_memory_rejected(F):
+    import torch
+    A = torch.ones(64, 64)
+    B = torch.ones(64, 64)
+    C = torch.zeros(64, 64)
+    p = F.Plan(64, 64, 64, host_operands=1, depth=1)
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_gemm(p.handle, 1.0, A.data_ptr(), B.data_ptr(), 0.0, C.data_ptr())
+    assert ei.value.status == 1
+    p.close()
