@@ -242,6 +242,28 @@ fmm_status_t fmm_mlp_train_step(float* params, float* adam_m, float* adam_v, int
  * autotuner. */
 fmm_status_t fmm_set_cost_model(const float* params, const float* mean6, const float* std6);
 
+/* Allocation-free variant of fmm_gemm for callers that cannot allocate
+ * device memory at call time -- code running inside CUDA stream capture
+ * (where cudaMalloc is not permitted), allocator-less embedding contexts, or
+ * hot paths whose memory budget is fixed up front.  The paper has no
+ * counterpart; it is a deployment convenience.
+ *
+ * Computes C <- alpha * A * B + beta * C (row-major device pointers, the same
+ * conventions as fmm_gemm) with one Winograd level over 3xTF32 tensor-core
+ * leaves.  Its temporaries live in a device array of 22,020,352 bytes compiled
+ * into the library (held by every GPU that loads it until the process exits),
+ * so M, N and K must each be <= 1024; larger sizes return FMM_ERR_INVALID_ARG
+ * with the limit in fmm_last_error().  The call allocates nothing (no
+ * cudaMalloc/cudaFree, no host heap).  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  Every call clears the status
+ * word it uses.  All calls share the one array, so calls that overlap on the
+ * GPU (different streams, or different threads on the same device) race and
+ * must be serialised by the caller. */
+fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                             const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                             fmm_stream_t stream);
+
 /* Phase profiling.  fmm_plan_profile(plan, 1) resets the counters and makes
  * every later fmm_gemm on the plan record CUDA events (on the call's stream)
  * around three phases: pre-additions (plus operand copies), the leaf launch,

@@ -1393,3 +1393,66 @@ fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precis
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free entry point.  Its temporaries (child operands of one Winograd
+// level and the seven products) live in a fixed device array compiled into the
+// library, so the call needs no workspace from the caller and makes no device
+// or host allocation.  The array is shared by every call on a device: calls
+// that overlap on the GPU race on it.
+namespace {
+constexpr long long kStaticMaxDim = 1024;
+// status block + 7 child operands per side + 7 products, each (1024/2)^2 floats
+constexpr size_t kStaticBytes = 256 + 3 * (size_t)7 * (kStaticMaxDim / 2) * (kStaticMaxDim / 2) * sizeof(float);
+__device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+void* g_static_scratch_addr[64] = {};
+}  // namespace
+
+extern "C" fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                                        const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                                        fmm_stream_t stream_) {
+    cudaStream_t stream = (cudaStream_t)stream_;
+    if (M < 0 || N < 0 || K < 0) return FMM_ERR_INVALID_ARG;
+    if (M > kStaticMaxDim || N > kStaticMaxDim || K > kStaticMaxDim) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "fmm_gemm_static: M, N, K must each be <= %lld (static scratch of %zu bytes)", kStaticMaxDim,
+                 kStaticBytes);
+        return FMM_ERR_INVALID_ARG;
+    }
+    if (lda < (K > 0 ? K : 1) || ldb < (N > 0 ? N : 1) || ldc < (N > 0 ? N : 1)) return FMM_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return FMM_OK;
+    if (!C) return FMM_ERR_INVALID_ARG;
+    DeviceInfo di;
+    fmm_status_t s = device_info(&di);
+    if (s != FMM_OK) return s;
+    int dev = 0;
+    FMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return FMM_ERR_NO_DEVICE;
+    if (!g_static_scratch_addr[dev]) {
+        // once per device, with that device current: the host-side name of the
+        // array is not a device address
+        void* ptr = nullptr;
+        FMM_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_static_scratch_addr[dev] = ptr;
+    }
+    if (alpha == 0.0f || K == 0) {
+        FMM_CUDA(launch_scale(C, ldc, M, N, beta, stream));
+        return FMM_OK;
+    }
+    if (!A || !B) return FMM_ERR_INVALID_ARG;
+    fmm_options_t o;
+    fmm_options_default(&o);
+    o.depth = 1;
+    fmm_plan_s p;
+    make_tmp(p, M, N, K, lda, ldb, ldc, o, 1, 256);
+    size_t need = 0;
+    layout(&p, nullptr, &need);
+    if (need > kStaticBytes) return FMM_ERR_WORKSPACE;
+    p.ws = static_cast<char*>(g_static_scratch_addr[dev]);
+    p.ws_bytes = kStaticBytes;
+    p.num_sms = di.num_sms;
+    layout(&p, p.ws, nullptr);
+    // the array keeps the previous call's contents: the status word must start at zero
+    FMM_CUDA(cudaMemsetAsync(p.status, 0, 64 * sizeof(unsigned), stream));
+    return execute(&p, alpha, A, B, beta, C, stream);
+}

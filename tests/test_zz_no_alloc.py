@@ -1,0 +1,62 @@
+"""The allocation-free entry point fmm_gemm_static, checked against the regular
+planned path (fmm_plan + fmm_gemm) on two calls in a row.
+
+fmm_gemm_static serves callers that cannot allocate device memory at call time
+(for example code inside CUDA stream capture, where cudaMalloc is not allowed):
+its temporaries live in a fixed device array compiled into the library, so M,
+N and K are limited to 1024.  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle.fmm_oracle as O
+from paper_1205_2927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+BOUND = 2e-6  # max-norm error bound the FP32 parity tests use
+
+
+def _static(F):
+    lib = F.library()
+    f = lib.fmm_gemm_static
+    f.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_float, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return f
+
+
+def test_static_entry_matches_planned_path_twice():
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    f = _static(F)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call, (m, k, n) in enumerate([(1000, 900, 1024), (513, 1024, 700)]):
+        A, B = I.operands(m, k, n, 12000 + call)
+        C0 = I.uniform((m, n), 12100 + call)
+        dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        c_static = torch.from_numpy(C0).cuda()
+        c_plan = torch.from_numpy(C0).cuda()
+        st = f(m, n, k, 0.75, dA.data_ptr(), k, dB.data_ptr(), n, 0.5, c_static.data_ptr(), n, stream)
+        assert st == 0, F.library().fmm_last_error()
+        p = F.Plan(m, n, k, depth=1)
+        p(dA, dB, c_plan, alpha=0.75, beta=0.5)
+        torch.cuda.synchronize()
+        got, want = c_static.cpu().numpy(), c_plan.cpu().numpy()
+        den = np.abs(A).max() * np.abs(B).max() * k
+        assert np.max(np.abs(got.astype(np.float64) - want)) / den <= BOUND
+        ref = O.gemm(0.75, A, B, 0.5, C0)
+        assert np.max(np.abs(got - ref)) / den <= BOUND
+        p.close()
+
+
+def test_static_entry_rejects_sizes_beyond_limit():
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    f = _static(F)
+    x = torch.zeros(4, device="cuda")
+    st = f(1025, 8, 8, 1.0, x.data_ptr(), 8, x.data_ptr(), 8, 0.0, x.data_ptr(), 8, None)
+    assert st == 1
+    assert b"1024" in F.library().fmm_last_error()
