@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-classical", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="square",
+                    choices=["square", "single1024", "sweep", "split", "batched", "planner"],
+                    help="square: the headline line; the others measure the other configurations")
+    ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     return ap.parse_args()
 
 
@@ -181,6 +185,220 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------------------- GPU legs
 
+def sampled_error(np, torch, dC, A_h, B_h, nrows=16, seed=1):
+    """max|C - C64| / (max|A| max|B| K) over `nrows` random rows; C64 rows by a
+    float64 matrix product on the host."""
+    m, k = A_h.shape
+    rows = np.sort(np.random.default_rng(seed).choice(m, size=min(nrows, m), replace=False))
+    C_rows = dC[torch.from_numpy(rows).to(dC.device)].cpu().numpy().astype(np.float64)
+    ref = A_h[rows].astype(np.float64) @ B_h.astype(np.float64)
+    return float(np.max(np.abs(C_rows - ref))) / (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * k)
+
+
+def emit(args, rec):
+    line = json.dumps(rec)
+    print(line, flush=True)
+    if args.out:
+        with open(args.out, "a") as f:
+            f.write(line + "\n")
+
+
+def event_ms(torch, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(steps):
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def wl_single1024(args):
+    """n = 1024, depth 2 (leaf 256), device-resident single call: median of 20 after 5 warm-ups."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    n = 1024
+    A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(1, 0))
+    dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+    dC = torch.empty((n, n), device="cuda")
+    for d in (0, 2):
+        p = fmm.Plan(n, n, n, depth=d)
+        ms = event_ms(torch, lambda: p(dA, dB, dC), 20, 5)
+        emit(args, {"workload": "single_n1024", "depth": d, "ms": round(ms, 4),
+                    "gflops": round(2 * n ** 3 / ms / 1e6, 1), "error": sampled_error(np, torch, dC, A_h, B_h, 64)})
+        p.close()
+
+
+def wl_sweep(args):
+    """n in {4096, 8192, 16384, 19000} x depth 0..4, U[-1,1] and N(0,1): device-resident
+    time and host-resident wall-clock (pinned operands, transfers inside), error on sampled rows."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    for n in (4096, 8192, 16384, 19000):
+        for dist in ("uniform", "normal"):
+            A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(2, n % 97), dist)
+            dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+            dC = torch.empty((n, n), device="cuda")
+            pA, pB = torch.from_numpy(A_h).pin_memory(), torch.from_numpy(B_h).pin_memory()
+            pC = torch.empty((n, n)).pin_memory()
+            for d in range(0, 5):
+                for odd in (("pad", "peel") if n == 19000 and d > 0 else ("pad",)):
+                    p = fmm.Plan(n, n, n, depth=d, odd=odd)
+                    ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 2)
+                    err = sampled_error(np, torch, dC, A_h, B_h)
+                    p.close()
+                    wall = None
+                    if odd == "pad" and dist == "uniform":
+                        hp = fmm.Plan(n, n, n, depth=d, host_operands=1)
+                        for _ in range(2):
+                            hp(pA, pB, pC)
+                        torch.cuda.synchronize()
+                        ws = []
+                        for _ in range(3):
+                            t0 = time.perf_counter()
+                            hp(pA, pB, pC)
+                            torch.cuda.current_stream().synchronize()
+                            ws.append((time.perf_counter() - t0) * 1e3)
+                        wall = sorted(ws)[1]
+                        hp.close()
+                    emit(args, {"workload": "sweep", "n": n, "depth": d, "odd": odd, "dist": dist,
+                                "device_ms": round(ms, 3), "device_gflops": round(2 * n ** 3 / ms / 1e6, 1),
+                                "host_wallclock_ms": round(wall, 3) if wall else None,
+                                "host_gflops": round(2 * n ** 3 / wall / 1e6, 1) if wall else None,
+                                "error": err})
+            del dA, dB, dC, pA, pB, pC
+            torch.cuda.empty_cache()
+
+
+def wl_split(args):
+    """Split-precision leaves: {fp32 (3xTF32), tf32, bf16x3, fp16x3} x depth 0..4 on
+    19000x12000x15000 and 16384^3, entries N(0,1) and log-uniform [1e-3, 1e3]; error
+    against a float64 product on sampled rows, and throughput."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    for (m, k, n) in ((19000, 12000, 15000), (16384, 16384, 16384)):
+        for dist in ("normal", "loguniform"):
+            A_h, B_h = inputs.operands(m, k, n, inputs.seed_for(3, m % 89), dist)
+            dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+            dC = torch.empty((m, n), device="cuda")
+            for prec in ("fp32", "tf32", "bf16x3", "fp16x3"):
+                for d in range(0, 5):
+                    p = fmm.Plan(m, n, k, depth=d, precision=prec)
+                    ms = event_ms(torch, lambda: p(dA, dB, dC), 2, 1)
+                    err = sampled_error(np, torch, dC, A_h, B_h)
+                    p.close()
+                    emit(args, {"workload": "split", "M": m, "K": k, "N": n, "dist": dist, "precision": prec,
+                                "depth": d, "ms": round(ms, 3), "gflops": round(2 * m * n * k / ms / 1e6, 1),
+                                "error": err, "finite": bool(torch.isfinite(dC).all().item())})
+            del dA, dB, dC
+            torch.cuda.empty_cache()
+
+
+def wl_batched(args):
+    """512 independent products, M, K, N log-uniform in [128, 4096] (multiples of 4),
+    U[-1,1]; one persistent leaf launch per replay of a CUDA graph; the leaf tile and the
+    per-problem depth cut-off are tuned by timing the whole batch."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    shapes = inputs.batched_shapes(512, inputs.seed_for(4, 0))
+    flops = sum(2.0 * m * k * n for m, k, n in shapes)
+    As = [torch.from_numpy(inputs.uniform((m, k), inputs.seed_for(4, 1) + 3 * i)).cuda() for i, (m, k, n) in enumerate(shapes)]
+    Bs = [torch.from_numpy(inputs.uniform((k, n), inputs.seed_for(4, 2) + 3 * i)).cuda() for i, (m, k, n) in enumerate(shapes)]
+    Cs = [torch.empty((m, n), device="cuda") for m, k, n in shapes]
+    best = None
+    t_tune0 = time.perf_counter()
+    for bn in (128, 256):
+        for cutoff in (1024, 2048, 8192):
+            bp = fmm.BatchedPlan(As, Bs, Cs, leaf_tile=bn, cutoff=cutoff)
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                bp.run(s)
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                bp.run(torch.cuda.current_stream())
+            ms = event_ms(torch, g.replay, 20, 3)
+            info = bp.info()
+            rec = {"workload": "batched512", "leaf_tile": bn, "cutoff": cutoff, "graph_replay_ms": round(ms, 3),
+                   "gflops": round(flops / ms / 1e6, 1), "total_flops": flops,
+                   "recursing_problems": int(sum(1 for d in info["depths"] if d > 0)),
+                   "leaf_tiles": info["total_tiles"]}
+            emit(args, rec)
+            if best is None or ms < best[0]:
+                best = (ms, bn, cutoff, g, bp)
+            else:
+                del g
+                bp.close()
+    tune_s = time.perf_counter() - t_tune0
+    ms, bn, cutoff, g, bp = best
+    g.replay()
+    torch.cuda.synchronize()
+    errs = []
+    for i in range(0, 512, 37):
+        A_h, B_h = As[i].cpu().numpy(), Bs[i].cpu().numpy()
+        ref = A_h.astype(np.float64) @ B_h.astype(np.float64)
+        errs.append(float(np.max(np.abs(Cs[i].cpu().numpy() - ref))) /
+                    (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * A_h.shape[1]))
+    emit(args, {"workload": "batched512_best", "leaf_tile": bn, "cutoff": cutoff, "graph_replay_ms": round(ms, 3),
+                "gflops": round(flops / ms / 1e6, 1), "tuning_s": round(tune_s, 2), "max_error_sampled": max(errs),
+                "launches_per_replay": "1 batched copy + pre/post of recursing problems + 1 persistent leaf launch"})
+
+
+def wl_planner(args):
+    """Learned planner: ~20k candidate timings on shapes of the other configurations,
+    network trained on the GPU, plans picked for 1000 unseen shapes; compared with
+    the exhaustive autotuner (planning time, chosen-plan GFLOPS) and the fixed rule."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    from paper_1205_2927_gb300 import planner as PL
+    rng = np.random.default_rng(inputs.seed_for(5, 0))
+    big = [(int(a), int(b), int(c)) for a, b, c in (rng.integers(1024, 4864, size=(60, 3)) * 4)]
+    train_shapes = inputs.batched_shapes(2300, inputs.seed_for(5, 1)) + big + [(16384, 16384, 16384), (19000, 12000, 15000)]
+    test_shapes = inputs.batched_shapes(1000, inputs.seed_for(5, 2))
+    t0 = time.perf_counter()
+    recs = PL.collect(train_shapes, reps=1, seed=5)
+    t_collect = time.perf_counter() - t0
+    X, y = PL.features(recs)
+    t0 = time.perf_counter()
+    params, mean, std, losses = PL.train(X, y, steps=3000, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    PL.save(os.path.join(ROOT, "gpurun_out", "cost_model.bin") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+            else "/tmp/cost_model.bin", params, mean, std)
+    PL.register(params, mean, std)
+    t0 = time.perf_counter()
+    test = PL.collect(test_shapes, reps=1, seed=6)
+    t_exhaustive = time.perf_counter() - t0
+    ev = PL.evaluate(test)
+    t0 = time.perf_counter()
+    for (M, K, N) in test_shapes[:200]:
+        PL.choice(M, N, K, "mlp")
+    t_mlp_plan = (time.perf_counter() - t0) / 200
+    fmm.fmm_set_cost_model(None)
+    s = PL.summary(ev)
+    emit(args, {"workload": "planner", "train_records": len(recs), "train_shapes": len(train_shapes),
+                "test_shapes": len(test_shapes), "final_train_loss": losses[-1][1],
+                "collect_s": round(t_collect, 1), "train_s": round(t_train, 2),
+                "exhaustive_plan_ms_per_shape": round(t_exhaustive / len(test_shapes) * 1e3, 2),
+                "mlp_plan_ms_per_shape": round(t_mlp_plan * 1e3, 3), **{k: (round(v, 4) if isinstance(v, float) else v)
+                                                                           for k, v in s.items()}})
+
+
+WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "split": wl_split, "batched": wl_batched,
+             "planner": wl_planner}
+
 def timed(torch, dist, world, fn, steps, warmup):
     for _ in range(warmup):
         fn()
@@ -209,6 +427,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload != "square":
+        WORKLOADS[args.workload](args)
         return
     import numpy as np
     import torch
@@ -247,12 +468,8 @@ def main():
     wplan.profile(False)
     assert wplan.device_status() == 0, "device status word set"
 
-    # accuracy of the benchmarked result on sampled rows against the float64 definition
-    from oracle import fmm_oracle as O  # test infrastructure: error check only
-    rows = np.random.default_rng(1).choice(n, size=16, replace=False)
-    C_rows = dC[torch.from_numpy(rows).cuda()].cpu().numpy()
-    ref_rows = O.classical_rows(A_h, B_h, rows)
-    err = float(np.max(np.abs(C_rows - ref_rows))) / (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * n)
+    # accuracy of the benchmarked result on sampled rows against a float64 product
+    err = sampled_error(np, torch, dC, A_h, B_h)
 
     classical = None
     if not args.no_classical:

@@ -28,11 +28,11 @@ MAGIC = b"FMMCOST1"
 def collect(shapes, reps=1, precision="fp32", seed=0, device="cuda"):
     """Time every candidate of every (M, K, N) shape.  Returns a list of dicts."""
     import torch
-    g = torch.Generator(device="cpu").manual_seed(seed)
+    g = torch.Generator(device=device).manual_seed(seed)
     recs = []
     for (M, K, N) in shapes:
-        A = (torch.rand((M, K), generator=g) * 2 - 1).to(device)
-        B = (torch.rand((K, N), generator=g) * 2 - 1).to(device)
+        A = torch.rand((M, K), generator=g, device=device) * 2 - 1
+        B = torch.rand((K, N), generator=g, device=device) * 2 - 1
         Cm = torch.empty((M, N), device=device)
         for d, t, ms in fmm.fmm_autotune(M, N, K, A, B, Cm, reps=reps, precision=precision):
             recs.append(dict(M=M, K=K, N=N, depth=d, tile=t, ms=float(ms), precision=precision))
