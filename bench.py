@@ -365,8 +365,10 @@ def wl_planner(args):
     from paper_1205_2927_gb300 import fmm, inputs
     from paper_1205_2927_gb300 import planner as PL
     rng = np.random.default_rng(inputs.seed_for(5, 0))
-    big = [(int(a), int(b), int(c)) for a, b, c in (rng.integers(1024, 4864, size=(60, 3)) * 4)]
-    train_shapes = inputs.batched_shapes(2300, inputs.seed_for(5, 1)) + big + [(16384, 16384, 16384), (19000, 12000, 15000)]
+    big = [(int(a), int(b), int(c)) for a, b, c in (rng.integers(1024, 4864, size=(160, 3)) * 4)]
+    squares = [(n, n, n) for n in (4096, 8192, 16384, 19000)]
+    train_shapes = (inputs.batched_shapes(5200, inputs.seed_for(5, 1)) + big + squares
+                    + [(19000, 12000, 15000), (16384, 16384, 16384)])
     test_shapes = inputs.batched_shapes(1000, inputs.seed_for(5, 2))
     t0 = time.perf_counter()
     recs = PL.collect(train_shapes, reps=1, seed=5)

@@ -13,6 +13,9 @@
 // All streaming kernels move 16-byte vectors when the view allows it.
 #include "fmm_internal.h"
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace fmm {
 
 namespace {
@@ -370,6 +373,140 @@ __global__ void __launch_bounds__(128) quad_post_kernel(QuadPost q) {
     }
 }
 
+// ---------------------------------------------------------------- 16-bit hi/lo planes
+// x * s = hi + lo (+ residual): hi = rn16(x s), lo = rn16(x s - hi) for four
+// values, stored as 4 x 16 bits into each plane.
+template <bool BF16>
+__device__ __forceinline__ void split_store16(uint16_t* hi, uint16_t* lo, float4 v, float sc) {
+    const float x0 = v.x * sc, x1 = v.y * sc, x2 = v.z * sc, x3 = v.w * sc;
+    uint32_t h01, h23, l01, l23;
+    if constexpr (BF16) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(x0, x1), b = __floats2bfloat162_rn(x2, x3);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        const __nv_bfloat162 c = __floats2bfloat162_rn(x0 - fa.x, x1 - fa.y), d = __floats2bfloat162_rn(x2 - fb.x, x3 - fb.y);
+        h01 = *reinterpret_cast<const uint32_t*>(&a); h23 = *reinterpret_cast<const uint32_t*>(&b);
+        l01 = *reinterpret_cast<const uint32_t*>(&c); l23 = *reinterpret_cast<const uint32_t*>(&d);
+    } else {
+        const __half2 a = __floats2half2_rn(x0, x1), b = __floats2half2_rn(x2, x3);
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        const __half2 c = __floats2half2_rn(x0 - fa.x, x1 - fa.y), d = __floats2half2_rn(x2 - fb.x, x3 - fb.y);
+        h01 = *reinterpret_cast<const uint32_t*>(&a); h23 = *reinterpret_cast<const uint32_t*>(&b);
+        l01 = *reinterpret_cast<const uint32_t*>(&c); l23 = *reinterpret_cast<const uint32_t*>(&d);
+    }
+    *reinterpret_cast<uint2*>(hi) = make_uint2(h01, h23);
+    *reinterpret_cast<uint2*>(lo) = make_uint2(l01, l23);
+}
+
+// Same arithmetic as pre_add_kernel (all 7 children), output split into planes.
+template <bool VEC, int SIDE_B, bool BF16>
+__global__ void __launch_bounds__(128) pre_add16_kernel(View P, long long h, long long w, Stack16 out,
+                                                        const float* __restrict__ scale) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= w) return;
+    const float sc = scale ? scale[SIDE_B] : 1.0f;
+    const long long node = blockIdx.z;
+    const float* base = P.ptr + node * P.node_stride;
+    const float* q1p = base + w;
+    const float* q2p = base + h * P.ld;
+    const float* q3p = q2p + w;
+    View v0 = P, v1 = P, v2 = P, v3 = P;
+    v1.valid_cols = P.valid_cols - w;
+    v2.valid_rows = P.valid_rows - h;
+    v3.valid_rows = P.valid_rows - h;
+    v3.valid_cols = P.valid_cols - w;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        const float4 Q0 = load_q<VEC>(v0, base, r, c);
+        const float4 Q1 = load_q<VEC>(v1, q1p, r, c);
+        const float4 Q2 = load_q<VEC>(v2, q2p, r, c);
+        const float4 Q3 = load_q<VEC>(v3, q3p, r, c);
+        float4 X1, X2, X3, X4;
+        if (!SIDE_B) {
+            X1 = add4(Q2, Q3); X2 = sub4(X1, Q0); X3 = sub4(Q0, Q2); X4 = sub4(Q1, X2);
+        } else {
+            X1 = sub4(Q2, Q0); X2 = sub4(Q3, X1); X3 = sub4(Q3, Q2); X4 = sub4(X2, Q1);
+        }
+        const float4 ch[7] = {Q0, Q1, SIDE_B ? Q3 : X4, SIDE_B ? X4 : Q3, X1, X2, X3};
+        const long long o = (node * out.nchild) * out.child_stride + r * out.ld + c;
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+            split_store16<BF16>(out.hi + o + i * out.child_stride, out.lo + o + i * out.child_stride, ch[i], sc);
+    }
+}
+
+// Root B side into 16-bit planes (transposing), children in product order.
+template <bool BF16>
+__global__ void __launch_bounds__(256) pre_add16_b_root_kernel(const float* __restrict__ B, long long ldb, long long K,
+                                                               long long N, long long kh, long long nh, Stack16 out,
+                                                               const float* __restrict__ scale) {
+    __shared__ float tile[7][32][33];
+    const float sc = scale ? scale[1] : 1.0f;
+    const long long k0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int kl = ty + 8 * i;
+        const long long k = k0 + kl, n = n0 + tx;
+        float b11 = 0.f, b12 = 0.f, b21 = 0.f, b22 = 0.f;
+        if (k < kh && n < nh) {
+            const long long kk2 = k + kh, nn2 = n + nh;
+            if (k < K && n < N) b11 = B[k * ldb + n];
+            if (k < K && nn2 < N) b12 = B[k * ldb + nn2];
+            if (kk2 < K && n < N) b21 = B[kk2 * ldb + n];
+            if (kk2 < K && nn2 < N) b22 = B[kk2 * ldb + nn2];
+        }
+        const float t1 = b12 - b11, t2 = b22 - t1, t3 = b22 - b12, t4 = t2 - b21;
+        tile[0][kl][tx] = b11; tile[1][kl][tx] = b21; tile[2][kl][tx] = b22; tile[3][kl][tx] = t4;
+        tile[4][kl][tx] = t1;  tile[5][kl][tx] = t2;  tile[6][kl][tx] = t3;
+    }
+    __syncthreads();
+    // each thread: 4 consecutive k of one n row, for the 7 children
+    const int t = ty * 32 + tx;          // 0..255
+    const int nl = t >> 3, kq = (t & 7) * 4;
+    const long long n = n0 + nl, k = k0 + kq;
+    if (n < nh && k < kh) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+            const float4 v = make_float4(tile[c][kq][nl], tile[c][kq + 1][nl], tile[c][kq + 2][nl], tile[c][kq + 3][nl]);
+            const long long o = c * out.child_stride + n * out.ld + k;
+            split_store16<BF16>(out.hi + o, out.lo + o, v, sc);
+        }
+    }
+}
+
+// Plain split (transpose = 0: rows x cols -> rows x ld planes) or transposed
+// split (transpose = 1: X is rows(K) x cols(N), planes are cols x ld).
+template <bool BF16, bool TRANS>
+__global__ void __launch_bounds__(256) split16_kernel(const float* __restrict__ X, long long ldx, long long rows,
+                                                      long long cols, Stack16 out, const float* __restrict__ scale,
+                                                      int which) {
+    __shared__ float tile[32][33];
+    const float sc = scale ? scale[which] : 1.0f;
+    const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long r = r0 + ty + 8 * i, c = c0 + tx;
+        tile[ty + 8 * i][tx] = (r < rows && c < cols) ? X[r * ldx + c] : 0.0f;
+    }
+    __syncthreads();
+    const int t = ty * 32 + tx;
+    const int a = t >> 3, q = (t & 7) * 4;   // output row a of the tile, 4 consecutive output columns
+    float4 v;
+    long long orow, ocol, olim_r, olim_c;
+    if (TRANS) {   // output (c, r): row = column of X
+        v = make_float4(tile[q][a], tile[q + 1][a], tile[q + 2][a], tile[q + 3][a]);
+        orow = c0 + a; ocol = r0 + q; olim_r = cols; olim_c = rows;
+    } else {
+        v = make_float4(tile[a][q], tile[a][q + 1], tile[a][q + 2], tile[a][q + 3]);
+        orow = r0 + a; ocol = c0 + q; olim_r = rows; olim_c = cols;
+    }
+    if (orow < olim_r && ocol < olim_c) {
+        // ld is a multiple of 8, so a group of 4 never crosses a row: padding columns get zeros
+        const long long o = orow * out.ld + ocol;
+        split_store16<BF16>(out.hi + o, out.lo + o, v, sc);
+    }
+}
+
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -468,6 +605,45 @@ cudaError_t launch_quad_post(const QuadPost& q, int part, cudaStream_t stream) {
     dim3 grid((unsigned)((q.w + 511) / 512), gy(q.h));
     if (part == 0) quad_post_kernel<0><<<grid, 128, 0, stream>>>(q);
     else quad_post_kernel<1><<<grid, 128, 0, stream>>>(q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add16(const View& parent, long long nodes, const Stack16& out, int side_b, int bf16,
+                             const float* scale, cudaStream_t stream) {
+    const long long h = parent.rows / 2, w = parent.cols / 2;
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    const bool vec = aligned16(parent.ptr) && parent.ld % 4 == 0 && w % 4 == 0 && parent.node_stride % 4 == 0;
+    dim3 grid((unsigned)((w + 4 * 128 - 1) / (4 * 128)), gy(h), (unsigned)nodes);
+#define FMM_PRE16(V, S, B) pre_add16_kernel<V, S, B><<<grid, 128, 0, stream>>>(parent, h, w, out, scale)
+    if (vec) {
+        if (side_b) { if (bf16) FMM_PRE16(true, 1, true); else FMM_PRE16(true, 1, false); }
+        else        { if (bf16) FMM_PRE16(true, 0, true); else FMM_PRE16(true, 0, false); }
+    } else {
+        if (side_b) { if (bf16) FMM_PRE16(false, 1, true); else FMM_PRE16(false, 1, false); }
+        else        { if (bf16) FMM_PRE16(false, 0, true); else FMM_PRE16(false, 0, false); }
+    }
+#undef FMM_PRE16
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add16_b_root(const float* B, long long ldb, long long K, long long N, long long kh,
+                                    long long nh, const Stack16& out, int bf16, const float* scale,
+                                    cudaStream_t stream) {
+    if (kh <= 0 || nh <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((nh + 31) / 32), (unsigned)((kh + 31) / 32));
+    if (bf16) pre_add16_b_root_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
+    else pre_add16_b_root_kernel<false><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split16(const float* X, long long ldx, long long rows, long long cols, const Stack16& out,
+                           int transpose, int bf16, const float* scale, int which, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+#define FMM_SPLIT(B, T) split16_kernel<B, T><<<grid, dim3(32, 8), 0, stream>>>(X, ldx, rows, cols, out, scale, which)
+    if (transpose) { if (bf16) FMM_SPLIT(true, true); else FMM_SPLIT(false, true); }
+    else           { if (bf16) FMM_SPLIT(true, false); else FMM_SPLIT(false, false); }
+#undef FMM_SPLIT
     return cudaGetLastError();
 }
 

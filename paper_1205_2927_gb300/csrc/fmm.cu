@@ -118,6 +118,26 @@ fmm_status_t encode_map(CUtensorMap* map, const float* base, long long cols, lon
     return FMM_OK;
 }
 
+// 3-D K-major 16-bit tile map (hi or lo plane): box {32, box_rows, 1}, 64-byte swizzle.
+fmm_status_t encode_map16(CUtensorMap* map, const uint16_t* base, bool bf16, long long cols, long long rows,
+                          long long batch, long long ld, long long batch_stride, int box_rows) {
+    if (cols <= 0 || rows <= 0 || batch <= 0) return FMM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || (batch_stride * 2) % 16) return FMM_ERR_ALIGNMENT;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(batch_stride * 2)};
+    cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                          const_cast<uint16_t*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled (16-bit) failed (%d)", (int)r);
+        return FMM_ERR_CUDA;
+    }
+    return FMM_OK;
+}
+
 struct Level {
     long long m, k, n;        // node operand sizes at this level
     long long nodes;          // 7^l
@@ -139,6 +159,11 @@ struct fmm_plan_s {
     long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
     int peel = 0;
     float border_beta = 0.f;
+    // split-precision plans: the leaf operands are written as 16-bit hi / lo planes
+    int pre16 = 0;
+    uint16_t* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
+    uint16_t* b16[2] = {};   // hi, lo planes of the leaf B^T operands
+    long long ld16 = 0;
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -219,7 +244,11 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         if (needed) *needed = align_up(cv.off, 256);
         return;
     }
-    if (d == 0) {
+    if (d == 0 && p->pre16) {
+        p->ld16 = rup(p->K, 8);
+        for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<uint16_t>((size_t)p->M * p->ld16);
+        for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<uint16_t>((size_t)p->N * p->ld16);
+    } else if (d == 0) {
         p->ld_bt = rup(p->K, 4);
         p->Bt = cv.take<float>((size_t)p->N * p->ld_bt);
         p->ld_acopy = rup(p->K, 4);
@@ -252,8 +281,14 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         for (int l = 0; l < d; ++l) {
             Level& L = p->lv[l];
             const Level& C = p->lv[l + 1];
-            L.full = (l < d - 1 || l == 0) ? 1 : 0;
+            L.full = (l < d - 1 || l == 0 || p->pre16) ? 1 : 0;
             const long long per = L.full ? 7 : 4;
+            if (p->pre16 && l == d - 1) {   // the leaves' operands, as 16-bit planes
+                p->ld16 = rup(C.k, 8);
+                for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<uint16_t>((size_t)(L.nodes * 7 * C.m * p->ld16));
+                for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<uint16_t>((size_t)(L.nodes * 7 * C.n * p->ld16));
+                continue;
+            }
             L.achild = cv.take<float>((size_t)(L.nodes * per * C.m * C.k));
             L.bchild = cv.take<float>((size_t)(L.nodes * per * C.n * C.k));
         }
@@ -325,7 +360,8 @@ int fixed_depth(long long M, long long N, long long K, int cutoff) {
 }
 
 // Leaf launch over `groups` (already filled except tile bookkeeping).
-fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream) {
+fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int mode = -1) {
+    if (mode < 0) mode = p->mode;
     long long t = 0;
     for (int g = 0; g < args.num_groups; ++g) {
         GemmGroup& G = args.groups[g];
@@ -338,16 +374,44 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream) {
     args.raster_m = 16;
     args.ext_maps = nullptr;
     args.ext_groups = nullptr;
-    if (p->mode == kLeafFP16x3)
+    if (mode == kLeafFP16x3 || mode == kLeafFP16x3P)
         for (int g = 0; g < args.num_groups; ++g) args.groups[g].scale = p->fp16_scale();
     args.status = p->status;
-    FMM_CUDA(launch_leaf_gemm(args, p->mode, p->bn, p->num_sms, stream));
+    FMM_CUDA(launch_leaf_gemm(args, mode, p->bn, p->num_sms, stream));
     p->launches += args.total_tiles > 0 ? 1 : 0;
     return FMM_OK;
 }
 
 fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                            cudaStream_t stream) {
+    if (p->pre16) {
+        const bool bf = p->mode == kLeafBF16x3P;
+        const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
+        const long long ld = p->ld16;
+        Stack16 sa{p->a16[0], p->a16[1], ld, 0, 1};
+        Stack16 sb{p->b16[0], p->b16[1], ld, 0, 1};
+        FMM_CUDA(launch_split16(A, p->lda, p->M, p->K, sa, 0, bf, scale, 0, stream));
+        FMM_CUDA(launch_split16(B, p->ldb, p->K, p->N, sb, 1, bf, scale, 1, stream));
+        p->launches += 2;
+        mark(p, 1, stream);
+        GemmArgs args;
+        memset(&args, 0, sizeof(args));
+        fmm_status_t s;
+        for (int i = 0; i < 2; ++i) {
+            if ((s = encode_map16(&args.maps[i], p->a16[i], bf, p->K, p->M, 1, ld, p->M * ld, kBM)) != FMM_OK) return s;
+            if ((s = encode_map16(&args.maps[2 + i], p->b16[i], bf, p->K, p->N, 1, ld, p->N * ld, p->bn)) != FMM_OK)
+                return s;
+        }
+        GemmGroup& G = args.groups[0];
+        G.M = (int)p->M; G.N = (int)p->N; G.K = (int)p->K; G.batch = 1;
+        G.C = C; G.ldc = p->ldc; G.alpha = alpha; G.beta = beta;
+        G.map_a = 0; G.map_a_lo = 1; G.map_b = 2; G.map_b_lo = 3;
+        G.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && p->ldc % 4 == 0) ? 1 : 0;
+        args.num_groups = 1;
+        s = run_leaves(p, args, stream);
+        mark(p, 2, stream);
+        return s;
+    }
     FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
     p->launches += 1;
     const float* Aop = A;
@@ -420,20 +484,31 @@ fmm_status_t run_border(fmm_plan_s* p, float alpha, const float* A, const float*
         return s;
     args.num_groups = ng;
     if (ng == 0) return FMM_OK;
-    return run_leaves(p, args, stream);
+    // the border reads fp32 operands: split-precision plans split them in shared memory
+    const int mode = p->mode == kLeafBF16x3P ? kLeafBF16x3 : (p->mode == kLeafFP16x3P ? kLeafFP16x3 : p->mode);
+    return run_leaves(p, args, stream, mode);
 }
 
 // Pre-additions of every level (breadth-first), reading the caller's A and B at the root.
 fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStream_t stream) {
     const int d = p->depth;
     Level* lv = p->lv;
+    const bool bf16 = p->mode == kLeafBF16x3P;
+    const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
     {
         const Level& C1 = lv[1];
         View va{A, p->lda, 0, lv[0].m, lv[0].k, p->Mw, p->Kw};
-        Stack sa{lv[0].achild, C1.k, C1.m * C1.k, 7};
-        FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
-        Stack sb{lv[0].bchild, C1.k, C1.n * C1.k, 7};
-        FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, 1, stream));
+        if (p->pre16 && d == 1) {
+            Stack16 sa{p->a16[0], p->a16[1], p->ld16, C1.m * p->ld16, 7};
+            Stack16 sb{p->b16[0], p->b16[1], p->ld16, C1.n * p->ld16, 7};
+            FMM_CUDA(launch_pre_add16(va, 1, sa, 0, bf16, scale, stream));
+            FMM_CUDA(launch_pre_add16_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, bf16, scale, stream));
+        } else {
+            Stack sa{lv[0].achild, C1.k, C1.m * C1.k, 7};
+            FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
+            Stack sb{lv[0].bchild, C1.k, C1.n * C1.k, 7};
+            FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, 1, stream));
+        }
         p->launches += 2;
     }
     for (int l = 1; l < d; ++l) {
@@ -442,6 +517,14 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         const Level& Pa = lv[l - 1];
         View va{Pa.achild, L.k, L.m * L.k, L.m, L.k, L.m, L.k};
         View vb{Pa.bchild, L.k, L.n * L.k, L.n, L.k, L.n, L.k};
+        if (p->pre16 && l == d - 1) {
+            Stack16 sa{p->a16[0], p->a16[1], p->ld16, Ch.m * p->ld16, 7};
+            Stack16 sb{p->b16[0], p->b16[1], p->ld16, Ch.n * p->ld16, 7};
+            FMM_CUDA(launch_pre_add16(va, L.nodes, sa, 0, bf16, scale, stream));
+            FMM_CUDA(launch_pre_add16(vb, L.nodes, sb, 1, bf16, scale, stream));
+            p->launches += 2;
+            continue;
+        }
         const int per = L.full ? 7 : 4;
         Stack sa{L.achild, Ch.k, Ch.m * Ch.k, per};
         Stack sb{L.bchild, Ch.k, Ch.n * Ch.k, per};
@@ -461,6 +544,23 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
     const Level& Ll = lv[d - 1];  // last recursion level
     fmm_status_t s;
     const long long mm = Lf.m, kk = Lf.k, nn = Lf.n;
+    if (p->pre16) {
+        const long long batch = Lf.nodes, ld = p->ld16;
+        const bool bf = p->mode == kLeafBF16x3P;
+        for (int i = 0; i < 2; ++i) {
+            if ((s = encode_map16(&maps[nm + i], p->a16[i], bf, kk, mm, batch, ld, mm * ld, kBM)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 2 + i], p->b16[i], bf, kk, nn, batch, ld, nn * ld, p->bn)) != FMM_OK)
+                return s;
+        }
+        GemmGroup& G = groups[ng++];
+        memset(&G, 0, sizeof(G));
+        G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)batch;
+        G.C = p->P; G.ldc = nn; G.c_batch_stride = mm * nn;
+        G.alpha = 1.f; G.beta = 0.f; G.map_a = nm; G.map_a_lo = nm + 1; G.map_b = nm + 2; G.map_b_lo = nm + 3;
+        G.vec_ok = 1;
+        nm += 4;
+        return FMM_OK;
+    }
     if (Ll.full) {
         const long long batch = Lf.nodes;
         if ((s = encode_map(&maps[nm], Ll.achild, kk, mm, batch, kk, mm * kk, kBM)) != FMM_OK) return s;
@@ -554,7 +654,7 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
 // One multiply with the plan's schedule (FP16x3 first derives its operand scales).
 fmm_status_t execute(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                      cudaStream_t stream) {
-    if (p->mode == kLeafFP16x3) {
+    if (p->mode == kLeafFP16x3 || p->mode == kLeafFP16x3P) {
         // operand magnitudes of the leaves are bounded by 4^depth times the root's
         const float bound = (float)(1LL << (2 * p->depth));
         FMM_CUDA(launch_fp16_scales(A, p->lda, p->M, p->K, B, p->ldb, p->N, bound, p->fp16_scale(),
@@ -746,6 +846,11 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
     }
     t.bn = bn;
     t.mode = leaf_mode(o.precision);
+    t.pre16 = 0;
+    if (!t.host && (o.precision == FMM_PREC_BF16X3 || o.precision == FMM_PREC_FP16X3)) {
+        t.pre16 = 1;
+        t.mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : kLeafFP16x3P;
+    }
 }
 
 size_t plan_bytes(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,

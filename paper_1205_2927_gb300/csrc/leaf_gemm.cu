@@ -30,12 +30,16 @@ namespace fmm {
 
 template <int BN, int MODE>
 struct LeafCfg {
-    static constexpr int kStages = (MODE == kLeafTF32) ? (BN == 256 ? 4 : 6) : (BN == 256 ? 2 : 3);
+    // pre-split stages hold A hi|lo and B hi|lo 16-bit tiles: as many bytes as one fp32 stage
+    static constexpr int kStages = (MODE == kLeafTF32 || MODE == kLeafBF16x3P || MODE == kLeafFP16x3P)
+                                       ? (BN == 256 ? 4 : 6)
+                                       : (BN == 256 ? 2 : 3);
     static constexpr int kABytes = kBM * 128;
     static constexpr int kBBytes = BN * 128;
     static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr bool kSplit = MODE != kLeafTF32;   // split warps + a second buffer per stage
-    static constexpr bool k16 = MODE == kLeafBF16x3 || MODE == kLeafFP16x3;
+    static constexpr bool kPre = MODE == kLeafBF16x3P || MODE == kLeafFP16x3P;  // 16-bit planes via TMA
+    static constexpr bool kSplit = MODE != kLeafTF32 && !kPre;   // split warps + a second buffer per stage
+    static constexpr bool k16 = MODE == kLeafBF16x3 || MODE == kLeafFP16x3 || kPre;
     static constexpr int kLoBytes = kSplit ? kStageBytes : 0;
     static constexpr int kTmemCols = 2 * BN;
     static constexpr int kThreads = kSplit ? 384 : 256;
@@ -153,8 +157,18 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     mbar_arrive_expect_tx(full_bar(stage), Cfg::kStageBytes);
                     const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
-                    tma_load_3d(sa, ma, full_bar(stage), kb * kBK, tm * kBM, b + G.a_batch_off);
-                    tma_load_3d(sa + Cfg::kABytes, mb, full_bar(stage), kb * kBK, tn * BN, b + G.b_batch_off);
+                    if constexpr (Cfg::kPre) {
+                        // A hi | B hi | A lo | B lo, 32 16-bit elements of K per row
+                        const uint32_t bh = sa + kBM * 64, al = bh + BN * 64, bl = al + kBM * 64;
+                        const int a0 = tm * kBM, b0 = tn * BN, ab = b + G.a_batch_off, bb = b + G.b_batch_off;
+                        tma_load_3d(sa, ma, full_bar(stage), kb * kBK, a0, ab);
+                        tma_load_3d(bh, mb, full_bar(stage), kb * kBK, b0, bb);
+                        tma_load_3d(al, maps + G.map_a_lo, full_bar(stage), kb * kBK, a0, ab);
+                        tma_load_3d(bl, maps + G.map_b_lo, full_bar(stage), kb * kBK, b0, bb);
+                    } else {
+                        tma_load_3d(sa, ma, full_bar(stage), kb * kBK, tm * kBM, b + G.a_batch_off);
+                        tma_load_3d(sa + Cfg::kABytes, mb, full_bar(stage), kb * kBK, tn * BN, b + G.b_batch_off);
+                    }
                     if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -163,7 +177,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = make_idesc(2u, kBM, BN);
-            constexpr uint32_t idesc16 = make_idesc(MODE == kLeafBF16x3 ? 1u : 0u, kBM, BN);
+            constexpr uint32_t idesc16 = make_idesc((MODE == kLeafBF16x3 || MODE == kLeafBF16x3P) ? 1u : 0u, kBM, BN);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -183,8 +197,9 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                     const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
                     const uint32_t sb = sa + Cfg::kABytes;
                     if constexpr (Cfg::k16) {
-                        // 16-bit hi/lo tiles, 64-byte rows: A hi | B hi | A lo | B lo
-                        const uint32_t ah = lo0 + stage * Cfg::kStageBytes;
+                        // 16-bit hi/lo tiles, 64-byte rows: A hi | B hi | A lo | B lo (in the
+                        // split buffer, or straight from TMA in the stage for pre-split planes)
+                        const uint32_t ah = (Cfg::kPre ? stage0 : lo0) + stage * Cfg::kStageBytes;
                         const uint32_t bh = ah + kBM * 64;
                         const uint32_t al = bh + BN * 64;
                         const uint32_t bl = al + kBM * 64;
@@ -284,7 +299,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }
-    } else if (Cfg::k16 && warp >= 8) {
+    } else if (Cfg::k16 && !Cfg::kPre && warp >= 8) {
         // ------------------------------------------------ fp32 -> 16-bit hi/lo
         // Reads the 128-byte-swizzled fp32 stage and writes hi = rn16(s*x),
         // lo = rn16(s*x - hi) into 64-byte-swizzled K-major tiles (16-byte chunk
@@ -399,6 +414,8 @@ cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms
         case kLeafTF32: FMM_LEAF(kLeafTF32);
         case kLeafBF16x3: FMM_LEAF(kLeafBF16x3);
         case kLeafFP16x3: FMM_LEAF(kLeafFP16x3);
+        case kLeafBF16x3P: FMM_LEAF(kLeafBF16x3P);
+        case kLeafFP16x3P: FMM_LEAF(kLeafFP16x3P);
         default: FMM_LEAF(kLeaf3xTF32);
     }
 #undef FMM_LEAF

@@ -68,3 +68,13 @@ def test_pageable_host_memory_rejected(F):
         F.fmm_gemm(p.handle, 1.0, A.data_ptr(), B.data_ptr(), 0.0, C.data_ptr())
     assert ei.value.status == 1
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3", "tf32"])
+def test_host_resident_split_precision(F, prec):
+    m, k, n = 640, 512, 768
+    A = I.small_int((m, k), 14000, r=2)
+    B = I.small_int((k, n), 14100, r=2)
+    C = run_host(F, A, B, depth=2, precision=prec)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(C, ref)

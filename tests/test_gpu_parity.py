@@ -274,3 +274,15 @@ def test_split_precision_winograd_bounds(fmm, prec, dist, d):
     err = O.error_metric(C, O.classical(A, B), A, B)
     bound = {"bf16x3": 5e-5, "fp16x3": 2e-6, "tf32": 5e-5}[prec]
     assert err <= bound, err
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_split16_peel_and_strided(fmm, prec):
+    m, k, n = 517, 333, 389
+    A = I.small_int((m, k), 13000 + m, r=2)
+    B = I.small_int((k, n), 13100 + n, r=2)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    C, _ = run(fmm, A, B, depth=2, precision=prec, odd="peel")
+    assert np.array_equal(C, ref)
+    C, _ = run(fmm, A, B, depth=3, precision=prec, leaf_tile=128)
+    assert np.array_equal(C, ref)
