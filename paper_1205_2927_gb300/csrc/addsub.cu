@@ -12,6 +12,7 @@
 //   B side: Y0, Y1, Y3, T4, T1, T2, T3        (sums only: T1, T2, T3, T4)
 // All streaming kernels move 16-byte vectors when the view allows it.
 #include "fmm_internal.h"
+#include "ptx.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -374,13 +375,26 @@ __global__ void __launch_bounds__(128) quad_post_kernel(QuadPost q) {
 }
 
 // ---------------------------------------------------------------- 16-bit hi/lo planes
-// x * s = hi + lo (+ residual): hi = rn16(x s), lo = rn16(x s - hi) for four
-// values, stored as 4 x 16 bits into each plane.
-template <bool BF16>
-__device__ __forceinline__ void split_store16(uint16_t* hi, uint16_t* lo, float4 v, float sc) {
+// Split four consecutive values into the planes at element offset o.
+//   bf16 / fp16: x * s = hi + lo (+ residual), hi = rn16(x s), lo = rn16(x s - hi)
+//   tf32:        hi = x (the tensor core reads trunc_tf32(x)), lo = rn_tf32(x - trunc_tf32(x))
+template <int KIND>
+__device__ __forceinline__ void split_store(void* hi_plane, void* lo_plane, long long o, float4 v, float sc) {
+    if constexpr (KIND == kSplitTF32) {
+        float4 l;
+        l.x = tf32_round_rne(v.x - tf32_trunc(v.x));
+        l.y = tf32_round_rne(v.y - tf32_trunc(v.y));
+        l.z = tf32_round_rne(v.z - tf32_trunc(v.z));
+        l.w = tf32_round_rne(v.w - tf32_trunc(v.w));
+        *reinterpret_cast<float4*>(static_cast<float*>(hi_plane) + o) = v;
+        *reinterpret_cast<float4*>(static_cast<float*>(lo_plane) + o) = l;
+        return;
+    }
+    uint16_t* hi = static_cast<uint16_t*>(hi_plane) + o;
+    uint16_t* lo = static_cast<uint16_t*>(lo_plane) + o;
     const float x0 = v.x * sc, x1 = v.y * sc, x2 = v.z * sc, x3 = v.w * sc;
     uint32_t h01, h23, l01, l23;
-    if constexpr (BF16) {
+    if constexpr (KIND == kSplitBF16) {
         const __nv_bfloat162 a = __floats2bfloat162_rn(x0, x1), b = __floats2bfloat162_rn(x2, x3);
         const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
         const __nv_bfloat162 c = __floats2bfloat162_rn(x0 - fa.x, x1 - fa.y), d = __floats2bfloat162_rn(x2 - fb.x, x3 - fb.y);
@@ -398,7 +412,7 @@ __device__ __forceinline__ void split_store16(uint16_t* hi, uint16_t* lo, float4
 }
 
 // Same arithmetic as pre_add_kernel (all 7 children), output split into planes.
-template <bool VEC, int SIDE_B, bool BF16>
+template <bool VEC, int SIDE_B, int KIND>
 __global__ void __launch_bounds__(128) pre_add16_kernel(View P, long long h, long long w, Stack16 out,
                                                         const float* __restrict__ scale) {
     const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -428,13 +442,12 @@ __global__ void __launch_bounds__(128) pre_add16_kernel(View P, long long h, lon
         const float4 ch[7] = {Q0, Q1, SIDE_B ? Q3 : X4, SIDE_B ? X4 : Q3, X1, X2, X3};
         const long long o = (node * out.nchild) * out.child_stride + r * out.ld + c;
 #pragma unroll
-        for (int i = 0; i < 7; ++i)
-            split_store16<BF16>(out.hi + o + i * out.child_stride, out.lo + o + i * out.child_stride, ch[i], sc);
+        for (int i = 0; i < 7; ++i) split_store<KIND>(out.hi, out.lo, o + i * out.child_stride, ch[i], sc);
     }
 }
 
 // Root B side into 16-bit planes (transposing), children in product order.
-template <bool BF16>
+template <int KIND>
 __global__ void __launch_bounds__(256) pre_add16_b_root_kernel(const float* __restrict__ B, long long ldb, long long K,
                                                                long long N, long long kh, long long nh, Stack16 out,
                                                                const float* __restrict__ scale) {
@@ -467,15 +480,14 @@ __global__ void __launch_bounds__(256) pre_add16_b_root_kernel(const float* __re
 #pragma unroll
         for (int c = 0; c < 7; ++c) {
             const float4 v = make_float4(tile[c][kq][nl], tile[c][kq + 1][nl], tile[c][kq + 2][nl], tile[c][kq + 3][nl]);
-            const long long o = c * out.child_stride + n * out.ld + k;
-            split_store16<BF16>(out.hi + o, out.lo + o, v, sc);
+            split_store<KIND>(out.hi, out.lo, c * out.child_stride + n * out.ld + k, v, sc);
         }
     }
 }
 
 // Plain split (transpose = 0: rows x cols -> rows x ld planes) or transposed
 // split (transpose = 1: X is rows(K) x cols(N), planes are cols x ld).
-template <bool BF16, bool TRANS>
+template <int KIND, bool TRANS>
 __global__ void __launch_bounds__(256) split16_kernel(const float* __restrict__ X, long long ldx, long long rows,
                                                       long long cols, Stack16 out, const float* __restrict__ scale,
                                                       int which) {
@@ -502,8 +514,7 @@ __global__ void __launch_bounds__(256) split16_kernel(const float* __restrict__ 
     }
     if (orow < olim_r && ocol < olim_c) {
         // ld is a multiple of 8, so a group of 4 never crosses a row: padding columns get zeros
-        const long long o = orow * out.ld + ocol;
-        split_store16<BF16>(out.hi + o, out.lo + o, v, sc);
+        split_store<KIND>(out.hi, out.lo, orow * out.ld + ocol, v, sc);
     }
 }
 
@@ -608,41 +619,57 @@ cudaError_t launch_quad_post(const QuadPost& q, int part, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pre_add16(const View& parent, long long nodes, const Stack16& out, int side_b, int bf16,
+cudaError_t launch_pre_add16(const View& parent, long long nodes, const Stack16& out, int side_b, int kind,
                              const float* scale, cudaStream_t stream) {
     const long long h = parent.rows / 2, w = parent.cols / 2;
     if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
     const bool vec = aligned16(parent.ptr) && parent.ld % 4 == 0 && w % 4 == 0 && parent.node_stride % 4 == 0;
     dim3 grid((unsigned)((w + 4 * 128 - 1) / (4 * 128)), gy(h), (unsigned)nodes);
-#define FMM_PRE16(V, S, B) pre_add16_kernel<V, S, B><<<grid, 128, 0, stream>>>(parent, h, w, out, scale)
-    if (vec) {
-        if (side_b) { if (bf16) FMM_PRE16(true, 1, true); else FMM_PRE16(true, 1, false); }
-        else        { if (bf16) FMM_PRE16(true, 0, true); else FMM_PRE16(true, 0, false); }
-    } else {
-        if (side_b) { if (bf16) FMM_PRE16(false, 1, true); else FMM_PRE16(false, 1, false); }
-        else        { if (bf16) FMM_PRE16(false, 0, true); else FMM_PRE16(false, 0, false); }
+#define FMM_PRE16(V, S, K) pre_add16_kernel<V, S, K><<<grid, 128, 0, stream>>>(parent, h, w, out, scale)
+#define FMM_PRE16K(V, S)                                                    \
+    switch (kind) {                                                          \
+        case kSplitBF16: FMM_PRE16(V, S, kSplitBF16); break;                \
+        case kSplitFP16: FMM_PRE16(V, S, kSplitFP16); break;                \
+        default: FMM_PRE16(V, S, kSplitTF32); break;                        \
     }
+    if (vec) { if (side_b) { FMM_PRE16K(true, 1) } else { FMM_PRE16K(true, 0) } }
+    else     { if (side_b) { FMM_PRE16K(false, 1) } else { FMM_PRE16K(false, 0) } }
+#undef FMM_PRE16K
 #undef FMM_PRE16
     return cudaGetLastError();
 }
 
 cudaError_t launch_pre_add16_b_root(const float* B, long long ldb, long long K, long long N, long long kh,
-                                    long long nh, const Stack16& out, int bf16, const float* scale,
+                                    long long nh, const Stack16& out, int kind, const float* scale,
                                     cudaStream_t stream) {
     if (kh <= 0 || nh <= 0) return cudaSuccess;
     dim3 grid((unsigned)((nh + 31) / 32), (unsigned)((kh + 31) / 32));
-    if (bf16) pre_add16_b_root_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
-    else pre_add16_b_root_kernel<false><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
+    switch (kind) {
+        case kSplitBF16:
+            pre_add16_b_root_kernel<kSplitBF16><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
+            break;
+        case kSplitFP16:
+            pre_add16_b_root_kernel<kSplitFP16><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
+            break;
+        default:
+            pre_add16_b_root_kernel<kSplitTF32><<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, kh, nh, out, scale);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_split16(const float* X, long long ldx, long long rows, long long cols, const Stack16& out,
-                           int transpose, int bf16, const float* scale, int which, cudaStream_t stream) {
+                           int transpose, int kind, const float* scale, int which, cudaStream_t stream) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-#define FMM_SPLIT(B, T) split16_kernel<B, T><<<grid, dim3(32, 8), 0, stream>>>(X, ldx, rows, cols, out, scale, which)
-    if (transpose) { if (bf16) FMM_SPLIT(true, true); else FMM_SPLIT(false, true); }
-    else           { if (bf16) FMM_SPLIT(true, false); else FMM_SPLIT(false, false); }
+#define FMM_SPLIT(K, T) split16_kernel<K, T><<<grid, dim3(32, 8), 0, stream>>>(X, ldx, rows, cols, out, scale, which)
+#define FMM_SPLITK(T)                                   \
+    switch (kind) {                                      \
+        case kSplitBF16: FMM_SPLIT(kSplitBF16, T); break; \
+        case kSplitFP16: FMM_SPLIT(kSplitFP16, T); break; \
+        default: FMM_SPLIT(kSplitTF32, T); break;         \
+    }
+    if (transpose) { FMM_SPLITK(true) } else { FMM_SPLITK(false) }
+#undef FMM_SPLITK
 #undef FMM_SPLIT
     return cudaGetLastError();
 }

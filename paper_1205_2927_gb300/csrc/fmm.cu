@@ -118,17 +118,21 @@ fmm_status_t encode_map(CUtensorMap* map, const float* base, long long cols, lon
     return FMM_OK;
 }
 
-// 3-D K-major 16-bit tile map (hi or lo plane): box {32, box_rows, 1}, 64-byte swizzle.
-fmm_status_t encode_map16(CUtensorMap* map, const uint16_t* base, bool bf16, long long cols, long long rows,
+// 3-D K-major tile map of a split plane: 64-byte rows (32 16-bit or 16 fp32
+// elements of K), box {row, box_rows, 1}, 64-byte swizzle.
+fmm_status_t encode_map16(CUtensorMap* map, const void* base, int kind, long long cols, long long rows,
                           long long batch, long long ld, long long batch_stride, int box_rows) {
     if (cols <= 0 || rows <= 0 || batch <= 0) return FMM_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || (batch_stride * 2) % 16) return FMM_ERR_ALIGNMENT;
+    const long long es = kind == kSplitTF32 ? 4 : 2;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * es) % 16 || (batch_stride * es) % 16) return FMM_ERR_ALIGNMENT;
     cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
-    cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(batch_stride * 2)};
-    cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, 1u};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(batch_stride * es)};
+    cuuint32_t box[3] = {(cuuint32_t)(64 / es), (cuuint32_t)box_rows, 1u};
     cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-                          const_cast<uint16_t*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUtensorMapDataType dt = kind == kSplitTF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUresult r = g_encode(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -159,11 +163,13 @@ struct fmm_plan_s {
     long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
     int peel = 0;
     float border_beta = 0.f;
-    // split-precision plans: the leaf operands are written as 16-bit hi / lo planes
+    // pre-split plans: the leaf operands are written as hi / lo planes (SplitKind)
     int pre16 = 0;
-    uint16_t* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
-    uint16_t* b16[2] = {};   // hi, lo planes of the leaf B^T operands
+    int split_kind = 0;
+    void* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
+    void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
+    size_t es16() const { return split_kind == kSplitTF32 ? 4 : 2; }
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -246,8 +252,8 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
     }
     if (d == 0 && p->pre16) {
         p->ld16 = rup(p->K, 8);
-        for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<uint16_t>((size_t)p->M * p->ld16);
-        for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<uint16_t>((size_t)p->N * p->ld16);
+        for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)p->M * p->ld16 * p->es16());
+        for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<char>((size_t)p->N * p->ld16 * p->es16());
     } else if (d == 0) {
         p->ld_bt = rup(p->K, 4);
         p->Bt = cv.take<float>((size_t)p->N * p->ld_bt);
@@ -285,8 +291,8 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             const long long per = L.full ? 7 : 4;
             if (p->pre16 && l == d - 1) {   // the leaves' operands, as 16-bit planes
                 p->ld16 = rup(C.k, 8);
-                for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<uint16_t>((size_t)(L.nodes * 7 * C.m * p->ld16));
-                for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<uint16_t>((size_t)(L.nodes * 7 * C.n * p->ld16));
+                for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
+                for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.n * p->ld16) * p->es16());
                 continue;
             }
             L.achild = cv.take<float>((size_t)(L.nodes * per * C.m * C.k));
@@ -385,7 +391,7 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int 
 fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                            cudaStream_t stream) {
     if (p->pre16) {
-        const bool bf = p->mode == kLeafBF16x3P;
+        const int bf = p->split_kind;
         const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
         const long long ld = p->ld16;
         Stack16 sa{p->a16[0], p->a16[1], ld, 0, 1};
@@ -485,7 +491,10 @@ fmm_status_t run_border(fmm_plan_s* p, float alpha, const float* A, const float*
     args.num_groups = ng;
     if (ng == 0) return FMM_OK;
     // the border reads fp32 operands: split-precision plans split them in shared memory
-    const int mode = p->mode == kLeafBF16x3P ? kLeafBF16x3 : (p->mode == kLeafFP16x3P ? kLeafFP16x3 : p->mode);
+    const int mode = p->mode == kLeafBF16x3P   ? kLeafBF16x3
+                     : p->mode == kLeafFP16x3P ? kLeafFP16x3
+                     : p->mode == kLeaf3xTF32P ? kLeaf3xTF32
+                                               : p->mode;
     return run_leaves(p, args, stream, mode);
 }
 
@@ -493,7 +502,7 @@ fmm_status_t run_border(fmm_plan_s* p, float alpha, const float* A, const float*
 fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStream_t stream) {
     const int d = p->depth;
     Level* lv = p->lv;
-    const bool bf16 = p->mode == kLeafBF16x3P;
+    const int kind = p->split_kind;
     const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
     {
         const Level& C1 = lv[1];
@@ -501,8 +510,8 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         if (p->pre16 && d == 1) {
             Stack16 sa{p->a16[0], p->a16[1], p->ld16, C1.m * p->ld16, 7};
             Stack16 sb{p->b16[0], p->b16[1], p->ld16, C1.n * p->ld16, 7};
-            FMM_CUDA(launch_pre_add16(va, 1, sa, 0, bf16, scale, stream));
-            FMM_CUDA(launch_pre_add16_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, bf16, scale, stream));
+            FMM_CUDA(launch_pre_add16(va, 1, sa, 0, kind, scale, stream));
+            FMM_CUDA(launch_pre_add16_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, kind, scale, stream));
         } else {
             Stack sa{lv[0].achild, C1.k, C1.m * C1.k, 7};
             FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
@@ -520,8 +529,8 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         if (p->pre16 && l == d - 1) {
             Stack16 sa{p->a16[0], p->a16[1], p->ld16, Ch.m * p->ld16, 7};
             Stack16 sb{p->b16[0], p->b16[1], p->ld16, Ch.n * p->ld16, 7};
-            FMM_CUDA(launch_pre_add16(va, L.nodes, sa, 0, bf16, scale, stream));
-            FMM_CUDA(launch_pre_add16(vb, L.nodes, sb, 1, bf16, scale, stream));
+            FMM_CUDA(launch_pre_add16(va, L.nodes, sa, 0, kind, scale, stream));
+            FMM_CUDA(launch_pre_add16(vb, L.nodes, sb, 1, kind, scale, stream));
             p->launches += 2;
             continue;
         }
@@ -546,7 +555,7 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
     const long long mm = Lf.m, kk = Lf.k, nn = Lf.n;
     if (p->pre16) {
         const long long batch = Lf.nodes, ld = p->ld16;
-        const bool bf = p->mode == kLeafBF16x3P;
+        const int bf = p->split_kind;
         for (int i = 0; i < 2; ++i) {
             if ((s = encode_map16(&maps[nm + i], p->a16[i], bf, kk, mm, batch, ld, mm * ld, kBM)) != FMM_OK) return s;
             if ((s = encode_map16(&maps[nm + 2 + i], p->b16[i], bf, kk, nn, batch, ld, nn * ld, p->bn)) != FMM_OK)
@@ -847,9 +856,14 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
     t.bn = bn;
     t.mode = leaf_mode(o.precision);
     t.pre16 = 0;
-    if (!t.host && (o.precision == FMM_PREC_BF16X3 || o.precision == FMM_PREC_FP16X3)) {
+    if (!t.host && o.precision != FMM_PREC_TF32) {
         t.pre16 = 1;
-        t.mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : kLeafFP16x3P;
+        t.split_kind = o.precision == FMM_PREC_BF16X3   ? kSplitBF16
+                       : o.precision == FMM_PREC_FP16X3 ? kSplitFP16
+                                                        : kSplitTF32;
+        t.mode = o.precision == FMM_PREC_BF16X3   ? kLeafBF16x3P
+                 : o.precision == FMM_PREC_FP16X3 ? kLeafFP16x3P
+                                                  : kLeaf3xTF32P;
     }
 }
 

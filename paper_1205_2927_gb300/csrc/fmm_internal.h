@@ -49,7 +49,7 @@ struct GemmArgs {
 // kLeafBF16x3 / kLeafFP16x3 split fp32 tiles in shared memory; the *P modes
 // read operands already split into 16-bit hi / lo planes in global memory.
 enum LeafMode : int { kLeafTF32 = 0, kLeaf3xTF32 = 1, kLeafBF16x3 = 2, kLeafFP16x3 = 3, kLeafBF16x3P = 4,
-                      kLeafFP16x3P = 5 };
+                      kLeafFP16x3P = 5, kLeaf3xTF32P = 6 };
 
 // Launch the persistent tensor-core leaf kernel.  Returns a cudaError_t.
 cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms, cudaStream_t stream);
@@ -132,29 +132,33 @@ struct QuadPost {
 };
 cudaError_t launch_quad_pre(const QuadPre& q, int side_b, cudaStream_t stream);
 cudaError_t launch_quad_post(const QuadPost& q, int part, cudaStream_t stream);
-// ------------------------------------------------------------ 16-bit hi/lo planes
-// A stack of 16-bit matrices split as x * s = hi + lo: child c of node p at
-// plane + (p * nchild + c) * child_stride, row stride ld (elements, multiple
-// of 8 so rows start on 16 bytes).
+// ------------------------------------------------------------ split hi/lo planes
+// Kinds of split: bf16 (x*s = hi + lo, 16-bit), fp16 (same, 16-bit), tf32
+// (fp32 planes: hi = x itself -- the tensor core reads trunc_tf32(x) -- and
+// lo = rn_tf32(x - trunc_tf32(x))).
+enum SplitKind : int { kSplitBF16 = 0, kSplitFP16 = 1, kSplitTF32 = 2 };
+// A stack of split matrices: child c of node p at plane + (p * nchild + c) *
+// child_stride elements, row stride ld (elements, multiple of 8 so rows start
+// on 16 bytes); element size 2 (bf16, fp16) or 4 (tf32).
 struct Stack16 {
-    uint16_t* hi;
-    uint16_t* lo;
+    void* hi;
+    void* lo;
     long long ld;
     long long child_stride;
     int nchild;
 };
 // Pre-additions of one level writing all 7 children as split 16-bit planes
 // (the last level of a split-precision plan); scale = device {s_a, s_b} or null.
-cudaError_t launch_pre_add16(const View& parent, long long nodes, const Stack16& out, int side_b, int bf16,
+cudaError_t launch_pre_add16(const View& parent, long long nodes, const Stack16& out, int side_b, int kind,
                              const float* scale, cudaStream_t stream);
 cudaError_t launch_pre_add16_b_root(const float* B, long long ldb, long long K, long long N, long long kh,
-                                    long long nh, const Stack16& out, int bf16, const float* scale,
+                                    long long nh, const Stack16& out, int kind, const float* scale,
                                     cudaStream_t stream);
 // Plain split of an M x K matrix (transpose = 0) or of B^T for a K x N matrix
 // B (transpose = 1, rows = K, cols = N) into 16-bit planes; which = 0 uses
 // scale[0], 1 uses scale[1].
 cudaError_t launch_split16(const float* X, long long ldx, long long rows, long long cols, const Stack16& out,
-                           int transpose, int bf16, const float* scale, int which, cudaStream_t stream);
+                           int transpose, int kind, const float* scale, int which, cudaStream_t stream);
 // Deterministic pseudo-random fill of n floats in [-1, 1) (autotuner scratch).
 cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream);
 // Cost-model inference (mlp.cu): Y = f(X), `batch` rows of 6 features.

@@ -30,16 +30,19 @@ namespace fmm {
 
 template <int BN, int MODE>
 struct LeafCfg {
-    // pre-split stages hold A hi|lo and B hi|lo 16-bit tiles: as many bytes as one fp32 stage
-    static constexpr int kStages = (MODE == kLeafTF32 || MODE == kLeafBF16x3P || MODE == kLeafFP16x3P)
+    static constexpr bool kPre32 = MODE == kLeaf3xTF32P;                         // fp32 raw / lo planes via TMA
+    static constexpr bool kPre = MODE == kLeafBF16x3P || MODE == kLeafFP16x3P || kPre32;  // split planes via TMA
+    // pre-split stages hold A hi|lo and B hi|lo tiles with 64-byte rows: as many bytes as one fp32 stage
+    static constexpr int kStages = (MODE == kLeafTF32 || kPre)
                                        ? (BN == 256 ? 4 : 6)
                                        : (BN == 256 ? 2 : 3);
     static constexpr int kABytes = kBM * 128;
     static constexpr int kBBytes = BN * 128;
     static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr bool kPre = MODE == kLeafBF16x3P || MODE == kLeafFP16x3P;  // 16-bit planes via TMA
+    static constexpr int kKB = kPre32 ? 16 : 32;   // K elements per stage (one 64- or 128-byte row)
     static constexpr bool kSplit = MODE != kLeafTF32 && !kPre;   // split warps + a second buffer per stage
-    static constexpr bool k16 = MODE == kLeafBF16x3 || MODE == kLeafFP16x3 || kPre;
+    static constexpr bool k16 = MODE == kLeafBF16x3 || MODE == kLeafFP16x3 || MODE == kLeafBF16x3P ||
+                                MODE == kLeafFP16x3P;
     static constexpr int kLoBytes = kSplit ? kStageBytes : 0;
     static constexpr int kTmemCols = 2 * BN;
     static constexpr int kThreads = kSplit ? 384 : 256;
@@ -152,22 +155,22 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                 const GemmGroup& G = groups[g];
                 const CUtensorMap* ma = maps + G.map_a;
                 const CUtensorMap* mb = maps + G.map_b;
-                const int nk = (G.K + kBK - 1) / kBK;
+                const int nk = (G.K + Cfg::kKB - 1) / Cfg::kKB;
                 for (int kb = 0; kb < nk; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     mbar_arrive_expect_tx(full_bar(stage), Cfg::kStageBytes);
                     const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
                     if constexpr (Cfg::kPre) {
-                        // A hi | B hi | A lo | B lo, 32 16-bit elements of K per row
+                        // A hi | B hi | A lo | B lo, 64-byte rows (32 16-bit or 16 fp32 elements of K)
                         const uint32_t bh = sa + kBM * 64, al = bh + BN * 64, bl = al + kBM * 64;
                         const int a0 = tm * kBM, b0 = tn * BN, ab = b + G.a_batch_off, bb = b + G.b_batch_off;
-                        tma_load_3d(sa, ma, full_bar(stage), kb * kBK, a0, ab);
-                        tma_load_3d(bh, mb, full_bar(stage), kb * kBK, b0, bb);
-                        tma_load_3d(al, maps + G.map_a_lo, full_bar(stage), kb * kBK, a0, ab);
-                        tma_load_3d(bl, maps + G.map_b_lo, full_bar(stage), kb * kBK, b0, bb);
+                        tma_load_3d(sa, ma, full_bar(stage), kb * Cfg::kKB, a0, ab);
+                        tma_load_3d(bh, mb, full_bar(stage), kb * Cfg::kKB, b0, bb);
+                        tma_load_3d(al, maps + G.map_a_lo, full_bar(stage), kb * Cfg::kKB, a0, ab);
+                        tma_load_3d(bl, maps + G.map_b_lo, full_bar(stage), kb * Cfg::kKB, b0, bb);
                     } else {
-                        tma_load_3d(sa, ma, full_bar(stage), kb * kBK, tm * kBM, b + G.a_batch_off);
-                        tma_load_3d(sa + Cfg::kABytes, mb, full_bar(stage), kb * kBK, tn * BN, b + G.b_batch_off);
+                        tma_load_3d(sa, ma, full_bar(stage), kb * Cfg::kKB, tm * kBM, b + G.a_batch_off);
+                        tma_load_3d(sa + Cfg::kABytes, mb, full_bar(stage), kb * Cfg::kKB, tn * BN, b + G.b_batch_off);
                     }
                     if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
                 }
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
-                const int nk = (groups[g].K + kBK - 1) / kBK;
+                const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
@@ -196,6 +199,25 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                     tc_fence_after();
                     const uint32_t sa = stage0 + stage * Cfg::kStageBytes;
                     const uint32_t sb = sa + Cfg::kABytes;
+                    if constexpr (Cfg::kPre32) {
+                        // fp32 raw | lo tiles with 64-byte rows (16 elements of K): A raw | B raw | A lo | B lo
+                        const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
+                        const uint32_t bh = ah + kBM * 64;
+                        const uint32_t al = bh + BN * 64;
+                        const uint32_t bl = al + kBM * 64;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                            const uint64_t ahd = sdesc_kmajor_sw64(ah + kk * 32);
+                            const uint64_t bhd = sdesc_kmajor_sw64(bh + kk * 32);
+                            mma_tf32(d, sdesc_kmajor_sw64(al + kk * 32), bhd, idesc, first);  // lo_a * hi_b
+                            mma_tf32(d, ahd, sdesc_kmajor_sw64(bl + kk * 32), idesc, 1u);     // hi_a * lo_b
+                            mma_tf32(d, ahd, bhd, idesc, 1u);                                 // hi_a * hi_b
+                        }
+                        mma_commit(empty_bar(stage));
+                        if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                        continue;
+                    }
                     if constexpr (Cfg::k16) {
                         // 16-bit hi/lo tiles, 64-byte rows: A hi | B hi | A lo | B lo (in the
                         // split buffer, or straight from TMA in the stage for pre-split planes)
@@ -299,7 +321,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }
-    } else if (Cfg::k16 && !Cfg::kPre && warp >= 8) {
+    } else if (Cfg::k16 && !Cfg::kPre && warp >= 8) {  // in-kernel 16-bit split
         // ------------------------------------------------ fp32 -> 16-bit hi/lo
         // Reads the 128-byte-swizzled fp32 stage and writes hi = rn16(s*x),
         // lo = rn16(s*x - hi) into 64-byte-swizzled K-major tiles (16-byte chunk
@@ -313,7 +335,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
             const GemmGroup& G = groups[g];
-            const int nk = (G.K + kBK - 1) / kBK;
+            const int nk = (G.K + Cfg::kKB - 1) / Cfg::kKB;
             const float s_a = G.scale ? G.scale[0] : 1.0f;
             const float s_b = G.scale ? G.scale[1] : 1.0f;
             for (int kb = 0; kb < nk; ++kb) {
@@ -350,7 +372,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
         for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
-            const int nk = (groups[g].K + kBK - 1) / kBK;
+            const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
             for (int kb = 0; kb < nk; ++kb) {
                 bool w = mbar_wait(full_bar(stage), phase, abort_flag, status);
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
@@ -416,6 +438,7 @@ cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms
         case kLeafFP16x3: FMM_LEAF(kLeafFP16x3);
         case kLeafBF16x3P: FMM_LEAF(kLeafBF16x3P);
         case kLeafFP16x3P: FMM_LEAF(kLeafFP16x3P);
+        case kLeaf3xTF32P: FMM_LEAF(kLeaf3xTF32P);
         default: FMM_LEAF(kLeaf3xTF32);
     }
 #undef FMM_LEAF
