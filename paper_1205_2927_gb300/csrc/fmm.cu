@@ -1564,6 +1564,10 @@ extern "C" fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float a
     o.depth = 1;
     fmm_plan_s p;
     make_tmp(p, M, N, K, lda, ldb, ldc, o, 1, 256);
+    // leaves split their fp32 tiles in shared memory: the temporaries are then
+    // the 7 child operands per side and the 7 products, which the array holds
+    p.pre16 = 0;
+    p.mode = kLeaf3xTF32;
     size_t need = 0;
     layout(&p, nullptr, &need);
     if (need > kStaticBytes) return FMM_ERR_WORKSPACE;
