@@ -518,6 +518,109 @@ __global__ void __launch_bounds__(256) split16_kernel(const float* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------- two levels at once
+// The 7 children of an operand from its 4 quadrants, in product order, with
+// the same fp32 operations as pre_add_kernel (A: S1..S4; B^T: T1..T4).
+template <int SIDE_B>
+__device__ __forceinline__ void children7(const float4 (&Q)[4], float4 (&ch)[7]) {
+    float4 X1, X2, X3, X4;
+    if (!SIDE_B) {
+        X1 = add4(Q[2], Q[3]); X2 = sub4(X1, Q[0]); X3 = sub4(Q[0], Q[2]); X4 = sub4(Q[1], X2);
+    } else {
+        X1 = sub4(Q[2], Q[0]); X2 = sub4(Q[3], X1); X3 = sub4(Q[3], Q[2]); X4 = sub4(X2, Q[1]);
+    }
+    ch[0] = Q[0]; ch[1] = Q[1];
+    ch[2] = SIDE_B ? Q[3] : X4;
+    ch[3] = SIDE_B ? X4 : Q[3];
+    ch[4] = X1; ch[5] = X2; ch[6] = X3;
+}
+
+// Pre-additions of two consecutive levels in one pass: each node operand
+// (4h x 4w, a uniform stack) -> its 49 grandchildren (h x w), written as split
+// planes at stack index (node * 7 + i) * 7 + j.  Identical arithmetic to two
+// pre_add passes; the middle level is never stored.
+template <int SIDE_B, int KIND>
+__global__ void __launch_bounds__(128) pre_add2_kernel(View P, long long h, long long w, Stack16 out,
+                                                       const float* __restrict__ scale) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= w) return;
+    const float sc = scale ? scale[SIDE_B] : 1.0f;
+    const long long node = blockIdx.z;
+    const float* base = P.ptr + node * P.node_stride;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        // sub-block (a, b) of the node: quadrant (a / 2, b / 2), sub-quadrant (a % 2, b % 2)
+        float4 X[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                X[a][b] = __ldg(reinterpret_cast<const float4*>(base + (a * h + r) * P.ld + b * w + c));
+        // quadrant q of the node, sub-quadrant t: X[(q / 2) * 2 + t / 2][(q % 2) * 2 + t % 2]
+        const long long o0 = (node * 49) * out.child_stride + r * out.ld + c;
+        float4 C[4][7];   // child i's quadrant t (t = sub-quadrant position)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float4 Qt[4] = {X[(t >> 1)][(t & 1)], X[(t >> 1)][2 + (t & 1)], X[2 + (t >> 1)][(t & 1)],
+                                  X[2 + (t >> 1)][2 + (t & 1)]};
+            float4 ch[7];
+            children7<SIDE_B>(Qt, ch);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) C[t][i] = ch[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const float4 Qi[4] = {C[0][i], C[1][i], C[2][i], C[3][i]};
+            float4 g[7];
+            children7<SIDE_B>(Qi, g);
+#pragma unroll
+            for (int j = 0; j < 7; ++j) split_store<KIND>(out.hi, out.lo, o0 + (i * 7 + j) * out.child_stride, g[j], sc);
+        }
+    }
+}
+
+// Post-additions of two consecutive levels in one pass: for each node, its 49
+// grandchild products P[(node * 7 + i) * 7 + j] (h x w, row stride ld_in) ->
+// the node output (4h x 4w).  The children's quadrant values are formed with
+// the same U-chain as post_add_kernel, then the node's; results are identical
+// to two post_add passes and the middle level is never stored.
+__device__ __forceinline__ float4 uchain_quadrant(int q, float4 P1, float4 P2, float4 P3, float4 P4, float4 P5,
+                                                  float4 P6, float4 P7) {
+    if (q == 0) return add4(P1, P2);                          // U1
+    const float4 U2 = add4(P1, P6);
+    if (q == 1) return add4(add4(U2, P5), P3);                // U5 = (U2 + P5) + P3
+    const float4 U3 = add4(U2, P7);
+    if (q == 2) return sub4(U3, P4);                          // U6
+    return add4(U3, P5);                                      // U7
+}
+
+__global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict__ P, long long ld_in, long long cs,
+                                                        long long h, long long w, float* out, long long ld_out,
+                                                        long long out_ns) {
+    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (c >= w) return;
+    const long long node = blockIdx.z;
+    const float* base = P + node * 49 * cs;
+    float* o = out + node * out_ns;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        const float* pr = base + r * ld_in + c;
+        auto ld = [&](int i, int j) { return __ldg(reinterpret_cast<const float4*>(pr + (i * 7 + j) * cs)); };
+#pragma unroll 1
+        for (int t = 0; t < 4; ++t) {            // sub-quadrant of every child quadrant
+            float4 Ct[7];                         // child i's quadrant t
+#pragma unroll
+            for (int i = 0; i < 7; ++i)
+                Ct[i] = uchain_quadrant(t, ld(i, 0), ld(i, 1), ld(i, 2), ld(i, 3), ld(i, 4), ld(i, 5), ld(i, 6));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {        // node quadrant q, its sub-quadrant t
+                const float4 v = uchain_quadrant(q, Ct[0], Ct[1], Ct[2], Ct[3], Ct[4], Ct[5], Ct[6]);
+                const long long rr = (long long)((q >> 1) * 2 + (t >> 1)) * h + r;
+                const long long cc = (long long)((q & 1) * 2 + (t & 1)) * w + c;
+                *reinterpret_cast<float4*>(o + rr * ld_out + cc) = v;
+            }
+        }
+    }
+}
+
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -671,6 +774,37 @@ cudaError_t launch_split16(const float* X, long long ldx, long long rows, long l
     if (transpose) { FMM_SPLITK(true) } else { FMM_SPLITK(false) }
 #undef FMM_SPLITK
 #undef FMM_SPLIT
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& out, int side_b, int kind,
+                            const float* scale, cudaStream_t stream) {
+    const long long h = node.rows / 4, w = node.cols / 4;
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    if (!aligned16(node.ptr) || node.ld % 4 || w % 4 || node.node_stride % 4) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((w + 511) / 512), gy(h), (unsigned)nodes);
+#define FMM_PRE2(S, K) pre_add2_kernel<S, K><<<grid, 128, 0, stream>>>(node, h, w, out, scale)
+#define FMM_PRE2K(S)                                        \
+    switch (kind) {                                          \
+        case kSplitBF16: FMM_PRE2(S, kSplitBF16); break;    \
+        case kSplitFP16: FMM_PRE2(S, kSplitFP16); break;    \
+        default: FMM_PRE2(S, kSplitTF32); break;            \
+    }
+    if (side_b) { FMM_PRE2K(1) } else { FMM_PRE2K(0) }
+#undef FMM_PRE2K
+#undef FMM_PRE2
+    return cudaGetLastError();
+}
+
+cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
+                             long long w, float* out, long long ld_out, long long out_node_stride,
+                             cudaStream_t stream) {
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    if (!aligned16(P) || !aligned16(out) || ld_in % 4 || child_stride % 4 || w % 4 || ld_out % 4 ||
+        out_node_stride % 4)
+        return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((w + 511) / 512), gy(h), (unsigned)nodes);
+    post_add2_kernel<<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride);
     return cudaGetLastError();
 }
 

@@ -170,6 +170,10 @@ struct fmm_plan_s {
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
     size_t es16() const { return split_kind == kSplitTF32 ? 4 : 2; }
+    // depth >= 3: the last two levels of pre-additions (split-plane plans) and of
+    // post-additions run as one pass each; the middle level is never stored
+    bool fuse_pre() const { return pre16 && depth >= 3; }
+    bool fuse_post() const { return depth >= 3; }
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -289,7 +293,8 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             const Level& C = p->lv[l + 1];
             L.full = (l < d - 1 || l == 0 || p->pre16) ? 1 : 0;
             const long long per = L.full ? 7 : 4;
-            if (p->pre16 && l == d - 1) {   // the leaves' operands, as 16-bit planes
+            if (p->fuse_pre() && l == d - 2) continue;   // written by neither pass: fused away
+            if (p->pre16 && l == d - 1) {   // the leaves' operands, as split planes
                 p->ld16 = rup(C.k, 8);
                 for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
                 for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.n * p->ld16) * p->es16());
@@ -301,6 +306,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         const Level& Lf = p->lv[d];
         p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
         for (int l = 1; l < d; ++l) {
+            if (p->fuse_post() && l == d - 1) continue;   // fused away
             Level& L = p->lv[l];
             L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
         }
@@ -526,6 +532,16 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         const Level& Pa = lv[l - 1];
         View va{Pa.achild, L.k, L.m * L.k, L.m, L.k, L.m, L.k};
         View vb{Pa.bchild, L.k, L.n * L.k, L.n, L.k, L.n, L.k};
+        if (p->fuse_pre() && l == d - 2) {
+            // levels d-2 and d-1 at once: level-(d-2) node operands -> the leaf operands
+            const Level& Lf = lv[d];
+            Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 49};
+            Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 49};
+            FMM_CUDA(launch_pre_add2(va, L.nodes, sa, 0, kind, scale, stream));
+            FMM_CUDA(launch_pre_add2(vb, L.nodes, sb, 1, kind, scale, stream));
+            p->launches += 2;
+            break;
+        }
         if (p->pre16 && l == d - 1) {
             Stack16 sa{p->a16[0], p->a16[1], p->ld16, Ch.m * p->ld16, 7};
             Stack16 sb{p->b16[0], p->b16[1], p->ld16, Ch.n * p->ld16, 7};
@@ -624,7 +640,16 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
 fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cudaStream_t stream) {
     const int d = p->depth;
     Level* lv = p->lv;
-    for (int l = d - 1; l >= 0; --l) {
+    int top = d - 1;
+    if (p->fuse_post()) {
+        // levels d-1 and d-2 at once: leaf products -> level-(d-2) node outputs
+        const Level& L = lv[d - 2];
+        const Level& Lf = lv[d];
+        FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, L.nodes, Lf.m, Lf.n, L.cnode, L.n, L.m * L.n, stream));
+        p->launches += 1;
+        top = d - 3;
+    }
+    for (int l = top; l >= 0; --l) {
         const Level& L = lv[l];
         const Level& Ch = lv[l + 1];
         const float* in = (l == d - 1) ? p->P : lv[l + 1].cnode;

@@ -159,6 +159,17 @@ cudaError_t launch_pre_add16_b_root(const float* B, long long ldb, long long K, 
 // scale[0], 1 uses scale[1].
 cudaError_t launch_split16(const float* X, long long ldx, long long rows, long long cols, const Stack16& out,
                            int transpose, int kind, const float* scale, int which, cudaStream_t stream);
+// Two consecutive levels in one pass (middle level never stored; identical
+// arithmetic).  pre: node operands (4h x 4w, uniform stack `node`) -> the 49
+// grandchildren as split planes (child stride, ld of `out`).  post: 49
+// grandchild products per node (h x w, row stride ld_in, child stride) ->
+// node outputs (4h x 4w, row stride ld_out, node stride).  Both need 16-byte
+// aligned views with w a multiple of 4.
+cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& out, int side_b, int kind,
+                            const float* scale, cudaStream_t stream);
+cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
+                             long long w, float* out, long long ld_out, long long out_node_stride,
+                             cudaStream_t stream);
 // Deterministic pseudo-random fill of n floats in [-1, 1) (autotuner scratch).
 cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream);
 // Cost-model inference (mlp.cu): Y = f(X), `batch` rows of 6 features.

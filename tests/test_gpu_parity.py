@@ -286,3 +286,15 @@ def test_split16_peel_and_strided(fmm, prec):
     assert np.array_equal(C, ref)
     C, _ = run(fmm, A, B, depth=3, precision=prec, leaf_tile=128)
     assert np.array_equal(C, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32"])
+@pytest.mark.parametrize("m,k,n,d", [(1024, 1024, 1024, 4), (1100, 900, 1300, 4), (800, 1024, 640, 3)])
+def test_deep_recursion_bit_exact(fmm, prec, m, k, n, d):
+    # depth >= 3 runs the bottom two levels of additions as fused passes
+    A = I.small_int((m, k), 15000 + m + d, r=1)
+    B = I.small_int((k, n), 15100 + n + d, r=1)
+    C, info = run(fmm, A, B, depth=d, precision=prec)
+    assert info["depth"] == d
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(C, ref)
