@@ -583,39 +583,43 @@ __global__ void __launch_bounds__(128) pre_add2_kernel(View P, long long h, long
 // the node output (4h x 4w).  The children's quadrant values are formed with
 // the same U-chain as post_add_kernel, then the node's; results are identical
 // to two post_add passes and the middle level is never stored.
-__device__ __forceinline__ float4 uchain_quadrant(int q, float4 P1, float4 P2, float4 P3, float4 P4, float4 P5,
-                                                  float4 P6, float4 P7) {
-    if (q == 0) return add4(P1, P2);                          // U1
-    const float4 U2 = add4(P1, P6);
-    if (q == 1) return add4(add4(U2, P5), P3);                // U5 = (U2 + P5) + P3
-    const float4 U3 = add4(U2, P7);
-    if (q == 2) return sub4(U3, P4);                          // U6
-    return add4(U3, P5);                                      // U7
+__device__ __forceinline__ float uchain_quadrant(int q, float P1, float P2, float P3, float P4, float P5, float P6,
+                                                 float P7) {
+    if (q == 0) return P1 + P2;                               // U1
+    const float U2 = P1 + P6;
+    if (q == 1) return (U2 + P5) + P3;                        // U5 = U4 + P3, U4 = U2 + P5
+    const float U3 = U2 + P7;
+    if (q == 2) return U3 - P4;                               // U6
+    return U3 + P5;                                           // U7
 }
 
+// One element per thread: the 49 products of a position are loaded once.
 __global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict__ P, long long ld_in, long long cs,
                                                         long long h, long long w, float* out, long long ld_out,
                                                         long long out_ns) {
-    const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= w) return;
     const long long node = blockIdx.z;
     const float* base = P + node * 49 * cs;
     float* o = out + node * out_ns;
     for (long long r = blockIdx.y; r < h; r += gridDim.y) {
         const float* pr = base + r * ld_in + c;
-        auto ld = [&](int i, int j) { return __ldg(reinterpret_cast<const float4*>(pr + (i * 7 + j) * cs)); };
-#pragma unroll 1
+        float p[7][7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+#pragma unroll
+            for (int j = 0; j < 7; ++j) p[i][j] = __ldg(pr + (i * 7 + j) * cs);
+#pragma unroll
         for (int t = 0; t < 4; ++t) {            // sub-quadrant of every child quadrant
-            float4 Ct[7];                         // child i's quadrant t
+            float Ct[7];                          // child i's quadrant t
 #pragma unroll
             for (int i = 0; i < 7; ++i)
-                Ct[i] = uchain_quadrant(t, ld(i, 0), ld(i, 1), ld(i, 2), ld(i, 3), ld(i, 4), ld(i, 5), ld(i, 6));
+                Ct[i] = uchain_quadrant(t, p[i][0], p[i][1], p[i][2], p[i][3], p[i][4], p[i][5], p[i][6]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {        // node quadrant q, its sub-quadrant t
-                const float4 v = uchain_quadrant(q, Ct[0], Ct[1], Ct[2], Ct[3], Ct[4], Ct[5], Ct[6]);
                 const long long rr = (long long)((q >> 1) * 2 + (t >> 1)) * h + r;
                 const long long cc = (long long)((q & 1) * 2 + (t & 1)) * w + c;
-                *reinterpret_cast<float4*>(o + rr * ld_out + cc) = v;
+                o[rr * ld_out + cc] = uchain_quadrant(q, Ct[0], Ct[1], Ct[2], Ct[3], Ct[4], Ct[5], Ct[6]);
             }
         }
     }
@@ -803,7 +807,7 @@ cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_st
     if (!aligned16(P) || !aligned16(out) || ld_in % 4 || child_stride % 4 || w % 4 || ld_out % 4 ||
         out_node_stride % 4)
         return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((w + 511) / 512), gy(h), (unsigned)nodes);
+    dim3 grid((unsigned)((w + 127) / 128), gy(h), (unsigned)nodes);
     post_add2_kernel<<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride);
     return cudaGetLastError();
 }
