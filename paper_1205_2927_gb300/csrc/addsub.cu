@@ -625,6 +625,41 @@ __global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict_
     }
 }
 
+// Split jobs of a batched launch (one 32 x 32 tile per block, jobs found by
+// binary search on their first tile).
+template <int KIND>
+__global__ void __launch_bounds__(256) batched_split_kernel(const SplitJob* __restrict__ jobs, int njobs) {
+    __shared__ float tile[32][33];
+    const long long t = blockIdx.x;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    const SplitJob J = jobs[lo];
+    const long long local = t - J.tile_begin;
+    const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const long long r = r0 + ty + 8 * i, c = c0 + tx;
+        tile[ty + 8 * i][tx] = (r < J.rows && c < J.cols) ? J.src[r * J.lds + c] : 0.0f;
+    }
+    __syncthreads();
+    const int u = ty * 32 + tx;
+    const int a = u >> 3, q = (u & 7) * 4;
+    float4 v;
+    long long orow, ocol, lim_r, lim_c;
+    if (J.transpose) {
+        v = make_float4(tile[q][a], tile[q + 1][a], tile[q + 2][a], tile[q + 3][a]);
+        orow = c0 + a; ocol = r0 + q; lim_r = J.cols; lim_c = J.rows;
+    } else {
+        v = make_float4(tile[a][q], tile[a][q + 1], tile[a][q + 2], tile[a][q + 3]);
+        orow = r0 + a; ocol = c0 + q; lim_r = J.rows; lim_c = J.cols;
+    }
+    if (orow < lim_r && ocol < lim_c) split_store<KIND>(J.dst, J.lo, orow * J.ldd + ocol, v, 1.0f);
+}
+
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -809,6 +844,17 @@ cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_st
         return cudaErrorInvalidValue;
     dim3 grid((unsigned)((w + 127) / 128), gy(h), (unsigned)nodes);
     post_add2_kernel<<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_split(const SplitJob* jobs, int njobs, long long total_tiles, int kind,
+                                 cudaStream_t stream) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    switch (kind) {
+        case kSplitBF16: batched_split_kernel<kSplitBF16><<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs); break;
+        case kSplitFP16: batched_split_kernel<kSplitFP16><<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs); break;
+        default: batched_split_kernel<kSplitTF32><<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs);
+    }
     return cudaGetLastError();
 }
 

@@ -713,6 +713,9 @@ struct fmm_batched_s {
     CopyJob* d_jobs = nullptr;
     int njobs = 0;
     long long job_tiles = 0;
+    // pre-split leaves: split jobs instead of copy jobs
+    int pre = 0, split_kind = 0;
+    SplitJob* d_sjobs = nullptr;
     std::vector<fmm_plan_s*> subs;     // Winograd sub-plans (problems with depth >= 1)
     std::vector<int> sub_problem;
     std::vector<int> depth;            // per problem
@@ -738,6 +741,12 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     b->count = count;
     b->bn = o.leaf_tile ? o.leaf_tile : 256;
     b->mode = leaf_mode(o.precision);
+    b->pre = o.precision == FMM_PREC_FP32 || o.precision == FMM_PREC_BF16X3;
+    if (b->pre) {
+        b->split_kind = o.precision == FMM_PREC_BF16X3 ? kSplitBF16 : kSplitTF32;
+        b->mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : kLeaf3xTF32P;
+    }
+    const size_t es = b->split_kind == kSplitTF32 ? 4 : 2;
     // per-problem depth and resource counts
     int total_maps = 0, total_groups = 0, total_jobs = 0;
     b->depth.assign(count, 0);
@@ -749,12 +758,15 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
         const long long mn = std::min(std::min((long long)M[i], (long long)N[i]), (long long)K[i]);
         while (d > 0 && (mn >> d) < 64) --d;  // keep leaves at least 64 wide
         b->depth[i] = d;
-        if (d == 0) { total_maps += 2; total_groups += 1; total_jobs += 2; }
+        if (b->pre) { total_maps += 4; total_groups += 1; total_jobs += d == 0 ? 2 : 0; }
+        else if (d == 0) { total_maps += 2; total_groups += 1; total_jobs += 2; }
         else { total_maps += 14; total_groups += 7; }
     }
     b->d_maps = cv.take<CUtensorMap>(total_maps > 0 ? total_maps : 1);
     b->d_groups = cv.take<GemmGroup>(total_groups > 0 ? total_groups : 1);
     b->d_jobs = cv.take<CopyJob>(total_jobs > 0 ? total_jobs : 1);
+    b->d_sjobs = cv.take<SplitJob>(total_jobs > 0 ? total_jobs : 1);
+    std::vector<SplitJob> sjobs;
     std::vector<CUtensorMap> maps(total_maps > 0 ? total_maps : 1);
     std::vector<GemmGroup> groups(total_groups > 0 ? total_groups : 1);
     std::vector<CopyJob> jobs;
@@ -762,7 +774,29 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     for (int i = 0; i < count; ++i) {
         const int d = b->depth[i];
         if (d < 0) continue;
-        if (d == 0) {
+        if (d == 0 && b->pre) {
+            const long long ld = rup(K[i], 8);
+            void* ah = cv.take<char>((size_t)M[i] * ld * es);
+            void* al = cv.take<char>((size_t)M[i] * ld * es);
+            void* bh = cv.take<char>((size_t)N[i] * ld * es);
+            void* bl = cv.take<char>((size_t)N[i] * ld * es);
+            if (!ws) continue;
+            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], ah, al, ld, 0, (int)((K[i] + 31) / 32), 0});
+            sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 31) / 32), 1});
+            fmm_status_t s;
+            const int kd = b->split_kind;
+            if ((s = encode_map16(&maps[nm], ah, kd, K[i], M[i], 1, ld, M[i] * ld, kBM)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 1], al, kd, K[i], M[i], 1, ld, M[i] * ld, kBM)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 2], bh, kd, K[i], N[i], 1, ld, N[i] * ld, b->bn)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 3], bl, kd, K[i], N[i], 1, ld, N[i] * ld, b->bn)) != FMM_OK) return s;
+            GemmGroup& G = groups[ng++];
+            memset(&G, 0, sizeof(G));
+            G.M = (int)M[i]; G.N = (int)N[i]; G.K = (int)K[i]; G.batch = 1;
+            G.C = C[i]; G.ldc = ldc[i]; G.alpha = alpha[i]; G.beta = beta[i];
+            G.map_a = nm; G.map_a_lo = nm + 1; G.map_b = nm + 2; G.map_b_lo = nm + 3;
+            G.vec_ok = ((reinterpret_cast<uintptr_t>(C[i]) & 15) == 0 && ldc[i] % 4 == 0) ? 1 : 0;
+            nm += 4;
+        } else if (d == 0) {
             const long long ldt = rup(K[i], 4);
             float* Bt = cv.take<float>((size_t)N[i] * ldt);
             const float* Aop = A[i];
@@ -794,6 +828,8 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             tmp.bn = b->bn;
             tmp.mode = b->mode;
             tmp.peel = 0;
+            tmp.pre16 = b->pre;
+            tmp.split_kind = b->split_kind;
             size_t need = 0;
             layout(&tmp, nullptr, &need);
             char* sub_ws = cv.take<char>(need);
@@ -828,8 +864,14 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
         J.tile_begin = jt;
         jt += ((J.rows + 31) / 32) * (long long)J.tiles_c;
     }
-    b->njobs = (int)jobs.size();
+    for (auto& J : sjobs) {
+        J.tile_begin = jt;
+        jt += ((J.rows + 31) / 32) * (long long)J.tiles_c;
+    }
+    b->njobs = (int)(b->pre ? sjobs.size() : jobs.size());
     b->job_tiles = jt;
+    if (!sjobs.empty())
+        FMM_CUDA(cudaMemcpy(b->d_sjobs, sjobs.data(), sizeof(SplitJob) * sjobs.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * (nm > 0 ? nm : 1), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(b->d_groups, groups.data(), sizeof(GemmGroup) * (ng > 0 ? ng : 1), cudaMemcpyHostToDevice));
     if (!jobs.empty())
@@ -1294,7 +1336,8 @@ fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
     cudaStream_t stream = (cudaStream_t)stream_;
     fmm_status_t s;
     if (b->njobs > 0) {
-        FMM_CUDA(launch_batched_copy(b->d_jobs, b->njobs, b->job_tiles, stream));
+        if (b->pre) FMM_CUDA(launch_batched_split(b->d_sjobs, b->njobs, b->job_tiles, b->split_kind, stream));
+        else FMM_CUDA(launch_batched_copy(b->d_jobs, b->njobs, b->job_tiles, stream));
         b->launches += 1;
     }
     for (size_t j = 0; j < b->subs.size(); ++j) {

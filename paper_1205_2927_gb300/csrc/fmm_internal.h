@@ -111,6 +111,22 @@ struct CopyJob {
     int transpose;
 };
 cudaError_t launch_batched_copy(const CopyJob* jobs, int njobs, long long total_tiles, cudaStream_t stream);
+// Batched split into planes: like the copy jobs, but `dst` / `lo` are the hi /
+// lo planes of split `kind` (SplitKind; no operand scaling) and ldd is the
+// planes' row stride in elements.
+struct SplitJob {
+    const float* src;
+    long long lds;
+    long long rows, cols;
+    void* dst;
+    void* lo;
+    long long ldd;
+    long long tile_begin;
+    int tiles_c;
+    int transpose;
+};
+cudaError_t launch_batched_split(const SplitJob* jobs, int njobs, long long total_tiles, int kind,
+                                 cudaStream_t stream);
 // FP16x3 operand scales: scale[0] = 2^e_a, scale[1] = 2^e_b with the largest
 // e such that bound_mult * max|X| * 2^e <= 2^14 (1 when X is all zero); the
 // maxima are taken over the M x K / K x N operands (any leading dimension).

@@ -33,12 +33,13 @@ def _upload(probs):
     return As, Bs, Cs
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32"])
 @pytest.mark.parametrize("cutoff,bn", [(4096, 256), (64, 256), (64, 128)])
-def test_batched_bit_exact_small_int(F, cutoff, bn):
+def test_batched_bit_exact_small_int(F, cutoff, bn, prec):
     import torch
     probs = _problems(48, 9100, lo=16, hi=700, mult=1)
     As, Bs, Cs = _upload(probs)
-    bp = F.BatchedPlan(As, Bs, Cs, cutoff=cutoff, leaf_tile=bn)
+    bp = F.BatchedPlan(As, Bs, Cs, cutoff=cutoff, leaf_tile=bn, precision=prec)
     info = bp.info()
     if cutoff == 64:
         assert max(info["depths"]) >= 1  # some problems recurse
