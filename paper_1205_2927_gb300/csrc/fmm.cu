@@ -255,7 +255,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         return;
     }
     if (d == 0 && p->pre16) {
-        p->ld16 = rup(p->K, 8);
+        p->ld16 = rup(p->K, 128 / (long long)p->es16());   // 128-byte row pitch
         for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)p->M * p->ld16 * p->es16());
         for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<char>((size_t)p->N * p->ld16 * p->es16());
     } else if (d == 0) {
@@ -295,7 +295,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             const long long per = L.full ? 7 : 4;
             if (p->fuse_pre() && l == d - 2) continue;   // written by neither pass: fused away
             if (p->pre16 && l == d - 1) {   // the leaves' operands, as split planes
-                p->ld16 = rup(C.k, 8);
+                p->ld16 = rup(C.k, 128 / (long long)p->es16());   // 128-byte row pitch
                 for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
                 for (int i = 0; i < 2; ++i) p->b16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.n * p->ld16) * p->es16());
                 continue;
@@ -775,7 +775,7 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
         const int d = b->depth[i];
         if (d < 0) continue;
         if (d == 0 && b->pre) {
-            const long long ld = rup(K[i], 8);
+            const long long ld = rup(K[i], 128 / (long long)es);   // 128-byte row pitch
             void* ah = cv.take<char>((size_t)M[i] * ld * es);
             void* al = cv.take<char>((size_t)M[i] * ld * es);
             void* bh = cv.take<char>((size_t)N[i] * ld * es);
@@ -1383,7 +1383,7 @@ fmm_status_t fmm_options_default(fmm_options_t* o) {
     if (!o) return FMM_ERR_INVALID_ARG;
     memset(o, 0, sizeof(*o));
     o->depth = -1;
-    o->cutoff = 1024;
+    o->cutoff = 4096;
     o->leaf_tile = 0;
     o->precision = FMM_PREC_FP32;
     o->odd = FMM_ODD_PAD;
