@@ -218,8 +218,10 @@ __global__ void __launch_bounds__(128) post_add_kernel(const float* __restrict__
     }
 }
 
+// Bt (rows_out x cols_out, >= N x K) = B^T, zeros outside the N x K valid part.
 __global__ void __launch_bounds__(256) transpose_kernel(const float* __restrict__ B, long long ldb, long long K,
-                                                        long long N, float* __restrict__ Bt, long long ldt) {
+                                                        long long N, float* __restrict__ Bt, long long ldt,
+                                                        long long rows_out, long long cols_out) {
     __shared__ float tile[32][33];
     const long long k0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(256) transpose_kernel(const float* __restrict_
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const long long n = n0 + ty + 8 * i, k = k0 + tx;
-        if (n < N && k < K) Bt[n * ldt + k] = tile[tx][ty + 8 * i];
+        if (n < rows_out && k < cols_out) Bt[n * ldt + k] = tile[tx][ty + 8 * i];
     }
 }
 
@@ -539,7 +541,18 @@ __device__ __forceinline__ void children7(const float4 (&Q)[4], float4 (&ch)[7])
 // (4h x 4w, a uniform stack) -> its 49 grandchildren (h x w), written as split
 // planes at stack index (node * 7 + i) * 7 + j.  Identical arithmetic to two
 // pre_add passes; the middle level is never stored.
-template <int SIDE_B, int KIND>
+// 4 consecutive elements at (row, col) of a view, zero outside its valid window.
+template <bool VEC>
+__device__ __forceinline__ float4 load_sub(const View& v, const float* base, long long row, long long col) {
+    if (VEC && row < v.valid_rows && col + 3 < v.valid_cols)
+        return __ldg(reinterpret_cast<const float4*>(base + row * v.ld + col));
+    float t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = (row < v.valid_rows && col + j < v.valid_cols) ? __ldg(base + row * v.ld + col + j) : 0.0f;
+    return f4(t[0], t[1], t[2], t[3]);
+}
+
+template <bool VEC, int SIDE_B, int KIND>
 __global__ void __launch_bounds__(128) pre_add2_kernel(View P, long long h, long long w, Stack16 out,
                                                        const float* __restrict__ scale) {
     const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -554,7 +567,7 @@ __global__ void __launch_bounds__(128) pre_add2_kernel(View P, long long h, long
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-                X[a][b] = __ldg(reinterpret_cast<const float4*>(base + (a * h + r) * P.ld + b * w + c));
+                X[a][b] = load_sub<VEC>(P, base, a * h + r, b * w + c);
         // quadrant q of the node, sub-quadrant t: X[(q / 2) * 2 + t / 2][(q % 2) * 2 + t % 2]
         const long long o0 = (node * 49) * out.child_stride + r * out.ld + c;
         float4 C[4][7];   // child i's quadrant t (t = sub-quadrant position)
@@ -594,9 +607,12 @@ __device__ __forceinline__ float uchain_quadrant(int q, float P1, float P2, floa
 }
 
 // One element per thread: the 49 products of a position are loaded once.
+// ROOT: out is the caller's C: alpha / beta and the valid window apply.
+template <bool ROOT>
 __global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict__ P, long long ld_in, long long cs,
                                                         long long h, long long w, float* out, long long ld_out,
-                                                        long long out_ns) {
+                                                        long long out_ns, long long valid_rows, long long valid_cols,
+                                                        float alpha, float beta) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= w) return;
     const long long node = blockIdx.z;
@@ -619,7 +635,13 @@ __global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict_
             for (int q = 0; q < 4; ++q) {        // node quadrant q, its sub-quadrant t
                 const long long rr = (long long)((q >> 1) * 2 + (t >> 1)) * h + r;
                 const long long cc = (long long)((q & 1) * 2 + (t & 1)) * w + c;
-                o[rr * ld_out + cc] = uchain_quadrant(q, Ct[0], Ct[1], Ct[2], Ct[3], Ct[4], Ct[5], Ct[6]);
+                const float v = uchain_quadrant(q, Ct[0], Ct[1], Ct[2], Ct[3], Ct[4], Ct[5], Ct[6]);
+                if (!ROOT) {
+                    o[rr * ld_out + cc] = v;
+                } else if (rr < valid_rows && cc < valid_cols) {
+                    float* dst = o + rr * ld_out + cc;
+                    *dst = (beta != 0.0f) ? alpha * v + beta * *dst : alpha * v;
+                }
             }
         }
     }
@@ -713,10 +735,12 @@ cudaError_t launch_post_add(const float* P, long long ld_in, long long child_str
 }
 
 cudaError_t launch_transpose(const float* B, long long ldb, long long K, long long N, float* Bt, long long ldt,
-                             cudaStream_t stream) {
-    if (K <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32));
-    transpose_kernel<<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, Bt, ldt);
+                             cudaStream_t stream, long long rows_out, long long cols_out) {
+    if (rows_out < 0) rows_out = N;
+    if (cols_out < 0) cols_out = K;
+    if (rows_out <= 0 || cols_out <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((rows_out + 31) / 32), (unsigned)((cols_out + 31) / 32));
+    transpose_kernel<<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, Bt, ldt, rows_out, cols_out);
     return cudaGetLastError();
 }
 
@@ -820,16 +844,18 @@ cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& ou
                             const float* scale, cudaStream_t stream) {
     const long long h = node.rows / 4, w = node.cols / 4;
     if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
-    if (!aligned16(node.ptr) || node.ld % 4 || w % 4 || node.node_stride % 4) return cudaErrorInvalidValue;
+    if (w % 4) return cudaErrorInvalidValue;
+    const bool vec = aligned16(node.ptr) && node.ld % 4 == 0 && node.node_stride % 4 == 0;
     dim3 grid((unsigned)((w + 511) / 512), gy(h), (unsigned)nodes);
-#define FMM_PRE2(S, K) pre_add2_kernel<S, K><<<grid, 128, 0, stream>>>(node, h, w, out, scale)
-#define FMM_PRE2K(S)                                        \
-    switch (kind) {                                          \
-        case kSplitBF16: FMM_PRE2(S, kSplitBF16); break;    \
-        case kSplitFP16: FMM_PRE2(S, kSplitFP16); break;    \
-        default: FMM_PRE2(S, kSplitTF32); break;            \
+#define FMM_PRE2(V, S, K) pre_add2_kernel<V, S, K><<<grid, 128, 0, stream>>>(node, h, w, out, scale)
+#define FMM_PRE2K(V, S)                                        \
+    switch (kind) {                                             \
+        case kSplitBF16: FMM_PRE2(V, S, kSplitBF16); break;    \
+        case kSplitFP16: FMM_PRE2(V, S, kSplitFP16); break;    \
+        default: FMM_PRE2(V, S, kSplitTF32); break;            \
     }
-    if (side_b) { FMM_PRE2K(1) } else { FMM_PRE2K(0) }
+    if (vec) { if (side_b) { FMM_PRE2K(true, 1) } else { FMM_PRE2K(true, 0) } }
+    else     { if (side_b) { FMM_PRE2K(false, 1) } else { FMM_PRE2K(false, 0) } }
 #undef FMM_PRE2K
 #undef FMM_PRE2
     return cudaGetLastError();
@@ -837,13 +863,16 @@ cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& ou
 
 cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
                              long long w, float* out, long long ld_out, long long out_node_stride,
+                             long long valid_rows, long long valid_cols, float alpha, float beta,
                              cudaStream_t stream) {
     if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
-    if (!aligned16(P) || !aligned16(out) || ld_in % 4 || child_stride % 4 || w % 4 || ld_out % 4 ||
-        out_node_stride % 4)
-        return cudaErrorInvalidValue;
     dim3 grid((unsigned)((w + 127) / 128), gy(h), (unsigned)nodes);
-    post_add2_kernel<<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride);
+    if (valid_rows >= 0)
+        post_add2_kernel<true><<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride,
+                                                         valid_rows, valid_cols, alpha, beta);
+    else
+        post_add2_kernel<false><<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride,
+                                                          -1, -1, 1.f, 0.f);
     return cudaGetLastError();
 }
 

@@ -174,6 +174,10 @@ struct fmm_plan_s {
     // post-additions run as one pass each; the middle level is never stored
     bool fuse_pre() const { return pre16 && depth >= 3; }
     bool fuse_post() const { return depth >= 3; }
+    // depth 2: both levels at once from / into the caller's matrices
+    bool fuse_root_pre() const { return pre16 && depth == 2; }
+    bool fuse_root_post() const { return depth == 2; }
+    float* bt_root = nullptr;   // root-fused plans: B^T zero-padded to N0 x K0
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -294,6 +298,10 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             L.full = (l < d - 1 || l == 0 || p->pre16) ? 1 : 0;
             const long long per = L.full ? 7 : 4;
             if (p->fuse_pre() && l == d - 2) continue;   // written by neither pass: fused away
+            if (p->fuse_root_pre() && l == 0) {           // fused away; B^T of the root instead
+                p->bt_root = cv.take<float>((size_t)(p->N0 * p->K0));
+                continue;
+            }
             if (p->pre16 && l == d - 1) {   // the leaves' operands, as split planes
                 p->ld16 = rup(C.k, 128 / (long long)p->es16());   // 128-byte row pitch
                 for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
@@ -306,7 +314,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         const Level& Lf = p->lv[d];
         p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
         for (int l = 1; l < d; ++l) {
-            if (p->fuse_post() && l == d - 1) continue;   // fused away
+            if ((p->fuse_post() || p->fuse_root_post()) && l == d - 1) continue;   // fused away
             Level& L = p->lv[l];
             L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
         }
@@ -510,6 +518,20 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
     Level* lv = p->lv;
     const int kind = p->split_kind;
     const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
+    if (p->fuse_root_pre()) {
+        // both levels at once: root -> the 49 leaf operands; B goes through one
+        // zero-padded transposed copy so that both sides are K-major
+        const Level& Lf = lv[2];
+        FMM_CUDA(launch_transpose(B, p->ldb, p->Kw, p->Nw, p->bt_root, p->K0, stream, p->N0, p->K0));
+        View va{A, p->lda, 0, p->M0, p->K0, p->Mw, p->Kw};
+        View vb{p->bt_root, p->K0, 0, p->N0, p->K0, p->N0, p->K0};
+        Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 49};
+        Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 49};
+        FMM_CUDA(launch_pre_add2(va, 1, sa, 0, kind, scale, stream));
+        FMM_CUDA(launch_pre_add2(vb, 1, sb, 1, kind, scale, stream));
+        p->launches += 3;
+        return FMM_OK;
+    }
     {
         const Level& C1 = lv[1];
         View va{A, p->lda, 0, lv[0].m, lv[0].k, p->Mw, p->Kw};
@@ -641,11 +663,20 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
     const int d = p->depth;
     Level* lv = p->lv;
     int top = d - 1;
+    if (p->fuse_root_post()) {
+        // both levels at once: leaf products -> the caller's C (alpha, beta, valid window)
+        const Level& Lf = lv[2];
+        FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, 1, Lf.m, Lf.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
+                                  stream));
+        p->launches += 1;
+        return FMM_OK;
+    }
     if (p->fuse_post()) {
         // levels d-1 and d-2 at once: leaf products -> level-(d-2) node outputs
         const Level& L = lv[d - 2];
         const Level& Lf = lv[d];
-        FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, L.nodes, Lf.m, Lf.n, L.cnode, L.n, L.m * L.n, stream));
+        FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, L.nodes, Lf.m, Lf.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
+                                  0.f, stream));
         p->launches += 1;
         top = d - 3;
     }
@@ -1446,6 +1477,7 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
     layout(p, p->ws, nullptr);
     cudaError_t e = cudaMemsetAsync(p->status, 0, 64 * sizeof(unsigned), (cudaStream_t)stream);
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMemsetAsync(status)"); }
+
     if (p->host) {
         fmm_plan_s c;
         make_child(p, c);

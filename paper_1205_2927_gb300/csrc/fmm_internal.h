@@ -90,9 +90,10 @@ cudaError_t launch_post_add(const float* P, long long ld_in, long long child_str
                             long long w, float* out, long long ld_out, long long out_node_stride,
                             long long valid_rows, long long valid_cols, float alpha, float beta,
                             cudaStream_t stream);
-// Transposed copy: B (K x N, ldb) -> Bt (N x K, ldt).
+// Transposed copy: B (K x N, ldb) -> Bt (N x K, ldt).  With rows_out x cols_out
+// given (>= N x K), the whole padded extent is written, zeros outside N x K.
 cudaError_t launch_transpose(const float* B, long long ldb, long long K, long long N, float* Bt, long long ldt,
-                             cudaStream_t stream);
+                             cudaStream_t stream, long long rows_out = -1, long long cols_out = -1);
 // Plain copy of an M x K matrix into a buffer with another leading dimension.
 cudaError_t launch_copy2d(const float* A, long long lda, long long M, long long K, float* dst, long long ldd,
                           cudaStream_t stream);
@@ -176,15 +177,17 @@ cudaError_t launch_pre_add16_b_root(const float* B, long long ldb, long long K, 
 cudaError_t launch_split16(const float* X, long long ldx, long long rows, long long cols, const Stack16& out,
                            int transpose, int kind, const float* scale, int which, cudaStream_t stream);
 // Two consecutive levels in one pass (middle level never stored; identical
-// arithmetic).  pre: node operands (4h x 4w, uniform stack `node`) -> the 49
-// grandchildren as split planes (child stride, ld of `out`).  post: 49
-// grandchild products per node (h x w, row stride ld_in, child stride) ->
-// node outputs (4h x 4w, row stride ld_out, node stride).  Both need 16-byte
-// aligned views with w a multiple of 4.
+// arithmetic).  pre: node operands (4h x 4w, uniform stack `node`, reads
+// outside its valid window are zero) -> the 49 grandchildren as split planes
+// (child stride, ld of `out`); w must be a multiple of 4.  post: 49 grandchild
+// products per node (h x w, row stride ld_in, child stride) -> node outputs
+// (4h x 4w, row stride ld_out, node stride); valid_rows >= 0 marks the root:
+// C <- alpha * U + beta * C inside valid_rows x valid_cols.
 cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& out, int side_b, int kind,
                             const float* scale, cudaStream_t stream);
 cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
                              long long w, float* out, long long ld_out, long long out_node_stride,
+                             long long valid_rows, long long valid_cols, float alpha, float beta,
                              cudaStream_t stream);
 // Deterministic pseudo-random fill of n floats in [-1, 1) (autotuner scratch).
 cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream);

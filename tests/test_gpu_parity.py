@@ -121,7 +121,7 @@ def test_blas_semantics(fmm):
     B = I.small_int((k, n), 6, r=3)
     ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
     Cnan = np.full((m, n), np.nan, np.float32)
-    for d in (0, 1):
+    for d in (0, 1, 2, 3):
         C, _ = run(fmm, A, B, Cnan, alpha=2.0, beta=0.0, depth=d)
         assert np.array_equal(C, (2.0 * ref).astype(np.float32))
         C0 = I.small_int((m, n), 7, r=5)
