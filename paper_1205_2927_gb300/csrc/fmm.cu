@@ -166,6 +166,7 @@ struct fmm_plan_s {
     // pre-split plans: the leaf operands are written as hi / lo planes (SplitKind)
     int pre16 = 0;
     int split_kind = 0;
+    int pair = 0;        // leaves on CTA pairs (cta_group::2), 256 x 256 tiles
     void* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
@@ -349,7 +350,8 @@ fmm_status_t drain_profile(fmm_plan_s* p) {
 
 fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->depth < -1 || o->depth > 6) return FMM_ERR_INVALID_ARG;
-    if (o->leaf_tile != 0 && o->leaf_tile != 128 && o->leaf_tile != 256) return FMM_ERR_INVALID_ARG;
+    if (o->leaf_tile != 0 && o->leaf_tile != 128 && o->leaf_tile != 256 && o->leaf_tile != 512)
+        return FMM_ERR_INVALID_ARG;
     if (o->precision < FMM_PREC_FP32 || o->precision > FMM_PREC_FP16X3) return FMM_ERR_INVALID_ARG;
     if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL) return FMM_ERR_INVALID_ARG;
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
@@ -381,7 +383,27 @@ int fixed_depth(long long M, long long N, long long K, int cutoff) {
 
 // Leaf launch over `groups` (already filled except tile bookkeeping).
 fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int mode = -1) {
+    const bool pair = p->pair && mode < 0;   // the peel border (explicit mode) stays single-CTA
     if (mode < 0) mode = p->mode;
+    if (pair) {
+        long long t = 0;
+        for (int g = 0; g < args.num_groups; ++g) {
+            GemmGroup& G = args.groups[g];
+            G.tiles_m = (G.M + 255) / 256;
+            G.tiles_n = (G.N + 255) / 256;
+            G.tile_begin = t;
+            t += (long long)G.tiles_m * G.tiles_n * G.batch;
+            if (mode == kLeafFP16x3P) G.scale = p->fp16_scale();
+        }
+        args.total_tiles = t;
+        args.raster_m = 8;
+        args.ext_maps = nullptr;
+        args.ext_groups = nullptr;
+        args.status = p->status;
+        FMM_CUDA(launch_leaf_gemm_pair(args, mode, p->num_sms, stream));
+        p->launches += args.total_tiles > 0 ? 1 : 0;
+        return FMM_OK;
+    }
     long long t = 0;
     for (int g = 0; g < args.num_groups; ++g) {
         GemmGroup& G = args.groups[g];
@@ -419,7 +441,8 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
         fmm_status_t s;
         for (int i = 0; i < 2; ++i) {
             if ((s = encode_map16(&args.maps[i], p->a16[i], bf, p->K, p->M, 1, ld, p->M * ld, kBM)) != FMM_OK) return s;
-            if ((s = encode_map16(&args.maps[2 + i], p->b16[i], bf, p->K, p->N, 1, ld, p->N * ld, p->bn)) != FMM_OK)
+            if ((s = encode_map16(&args.maps[2 + i], p->b16[i], bf, p->K, p->N, 1, ld, p->N * ld,
+                                  p->pair ? 128 : p->bn)) != FMM_OK)
                 return s;
         }
         GemmGroup& G = args.groups[0];
@@ -596,7 +619,8 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
         const int bf = p->split_kind;
         for (int i = 0; i < 2; ++i) {
             if ((s = encode_map16(&maps[nm + i], p->a16[i], bf, kk, mm, batch, ld, mm * ld, kBM)) != FMM_OK) return s;
-            if ((s = encode_map16(&maps[nm + 2 + i], p->b16[i], bf, kk, nn, batch, ld, nn * ld, p->bn)) != FMM_OK)
+            if ((s = encode_map16(&maps[nm + 2 + i], p->b16[i], bf, kk, nn, batch, ld, nn * ld, p->pair ? 128 : p->bn)) !=
+                FMM_OK)
                 return s;
         }
         GemmGroup& G = groups[ng++];
@@ -770,7 +794,7 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     Carver cv(ws);
     b->status = cv.take<unsigned>(64);
     b->count = count;
-    b->bn = o.leaf_tile ? o.leaf_tile : 256;
+    b->bn = (o.leaf_tile && o.leaf_tile != 512) ? o.leaf_tile : 256;   // batched launches stay single-CTA
     b->mode = leaf_mode(o.precision);
     b->pre = o.precision == FMM_PREC_FP32 || o.precision == FMM_PREC_BF16X3;
     if (b->pre) {
@@ -954,7 +978,10 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
     t.bn = bn;
     t.mode = leaf_mode(o.precision);
     t.pre16 = 0;
+    t.pair = 0;
+    if (t.bn == 512) t.bn = 256;   // the pair tile is 256 wide: set below when the plan can use it
     if (!t.host && o.precision != FMM_PREC_TF32) {
+        t.pair = bn == 512 ? 1 : 0;
         t.pre16 = 1;
         t.split_kind = o.precision == FMM_PREC_BF16X3   ? kSplitBF16
                        : o.precision == FMM_PREC_FP16X3 ? kSplitFP16
@@ -1016,7 +1043,8 @@ void raw_features(long long M, long long N, long long K, int depth, int bn, int 
 void make_child(const fmm_plan_s* p, fmm_plan_s& c) {
     fmm_options_t o = p->opt;
     o.host_operands = 0;
-    make_tmp(c, p->hm, p->hn, p->hk, p->hk, p->hn, p->hn, o, p->depth > 0 ? p->depth - 1 : 0, p->bn);
+    make_tmp(c, p->hm, p->hn, p->hk, p->hk, p->hn, p->hn, o, p->depth > 0 ? p->depth - 1 : 0,
+             p->opt.leaf_tile == 512 ? 512 : p->bn);
 }
 
 // Host-resident multiply.  The root level runs depth-first over the seven
@@ -1604,7 +1632,7 @@ fmm_status_t fmm_get_device_status(fmm_plan_t p) {
 fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precision, int* odd, int* algo) {
     if (!p) return FMM_ERR_INVALID_ARG;
     if (depth) *depth = p->depth;
-    if (leaf_tile) *leaf_tile = p->bn;
+    if (leaf_tile) *leaf_tile = p->pair ? 512 : p->bn;
     if (precision) *precision = (int)p->opt.precision;
     if (odd) *odd = (int)p->opt.odd;
     if (algo) *algo = (int)p->opt.algo;

@@ -54,6 +54,10 @@ enum LeafMode : int { kLeafTF32 = 0, kLeaf3xTF32 = 1, kLeafBF16x3 = 2, kLeafFP16
 // Launch the persistent tensor-core leaf kernel.  Returns a cudaError_t.
 cudaError_t launch_leaf_gemm(const GemmArgs& args, int mode, int bn, int num_sms, cudaStream_t stream);
 size_t leaf_smem_bytes(int mode, int bn);
+// CTA-pair variant (pre-split modes only): 256 x 256 tiles (group tiles_m /
+// tiles_n must be counted in 256-row / 256-column units, B maps with 128-row
+// boxes).
+cudaError_t launch_leaf_gemm_pair(const GemmArgs& args, int mode, int num_sms, cudaStream_t stream);
 
 // ------------------------------------------------------------ additions
 // A matrix operand view: `nodes` matrices of rows x cols, node i at

@@ -402,6 +402,276 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Pair-of-SMs variant (cta_group::2) for the pre-split modes.  A cluster of two
+// CTAs computes one 256 x 256 output tile: CTA r (cluster rank) loads rows
+// [128 r, 128 r + 128) of the A tile and of the B^T tile into its own shared
+// memory; CTA 0 issues M = 256 tcgen05.mma instructions that read both CTAs'
+// halves, and each CTA's tensor memory holds its 128 rows of the accumulator.
+// Per SM this halves the B-operand shared-memory traffic of the single-CTA
+// kernel (operand reads + TMA writes 80 KB instead of 120 KB per K step).
+//   both CTAs  warp 0: TMA producer into local stages (local full barriers)
+//              warp 2: TMEM allocation, collective over the pair
+//              warp 3: forwards "stage landed" to CTA 0's ready barrier
+//              warps 4-7: epilogue of the local 128 rows; each thread then
+//                         arrives on CTA 0's accumulator-free barrier
+//   CTA 0      warp 1: MMA issuer; commits are multicast to both CTAs
+template <int MODE>
+struct PairCfg {
+    static constexpr int kRows = 128;                          // rows per CTA of A and of B^T
+    static constexpr int kStageBytes = 4 * kRows * 64;         // A hi | B hi | A lo | B lo, 64-byte rows
+    static constexpr int kStages = 6;
+    static constexpr int kKB = MODE == kLeaf3xTF32P ? 16 : 32; // K elements per 64-byte row
+    static constexpr int kTmemCols = 512;                      // 2 x 256-column accumulators
+    static constexpr int kBarBytes = 256;
+    static constexpr int kThreads = 256;
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kBarBytes;
+    static_assert((3 * kStages + 4) * 8 + 16 <= kBarBytes, "barrier area");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+template <int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
+    leaf_gemm_pair_kernel(const __grid_constant__ GemmArgs args) {
+    using Cfg = PairCfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    const uint32_t base = (raw_addr + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw_addr);
+    const uint32_t stage0 = base;
+    const uint32_t bar0 = base + Cfg::kStages * Cfg::kStageBytes;
+    uint8_t* bar_ptr = base_ptr + (bar0 - base);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 8 * (3 * Cfg::kStages + 4));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar_ptr + 8 * (3 * Cfg::kStages + 4) + 8);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (Cfg::kStages + s); };
+    auto ready_bar = [&](int s) { return bar0 + 8u * (2 * Cfg::kStages + s); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (3 * Cfg::kStages + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (3 * Cfg::kStages + 2 + a); };
+
+    const uint32_t rank = cluster_ctarank();
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const CUtensorMap* maps = args.ext_maps ? args.ext_maps : args.maps;
+    const GemmGroup* groups = args.ext_groups ? args.ext_groups : args.groups;
+    const int ng = args.num_groups;
+    const long long total = args.total_tiles;   // 256 x 256 pair tiles
+    const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    unsigned* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Cfg::kStages; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+            mbar_init(ready_bar(s), 2);    // one forwarded arrival per CTA (used in CTA 0)
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 256); // every epilogue thread of both CTAs (used in CTA 0)
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2) {
+        tmem_alloc_pair(smem_u32(tmem_slot), Cfg::kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // the peer's barriers are initialised before any remote arrival
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (long long t = pair; t < total && ok; t += npairs) {
+                int g, b, tm, tn;
+                decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+                const GemmGroup& G = groups[g];
+                const int nk = (G.K + Cfg::kKB - 1) / Cfg::kKB;
+                const int a0 = tm * 256 + (int)rank * Cfg::kRows, b0 = tn * 256 + (int)rank * Cfg::kRows;
+                const int ab = b + G.a_batch_off, bb = b + G.b_batch_off;
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                    mbar_arrive_expect_tx(full_bar(stage), Cfg::kStageBytes);
+                    const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
+                    const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+                    const int x = kb * Cfg::kKB;
+                    tma_load_3d(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
+                    tma_load_3d(bh, maps + G.map_b, full_bar(stage), x, b0, bb);
+                    tma_load_3d(al, maps + G.map_a_lo, full_bar(stage), x, a0, ab);
+                    tma_load_3d(bl, maps + G.map_b_lo, full_bar(stage), x, b0, bb);
+                    if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+        }
+    } else if (warp == 3) {
+        // ------------------------------------------------ forwarder (both CTAs)
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (long long t = pair; t < total && ok; t += npairs) {
+                int g, b, tm, tn;
+                decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+                const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
+                    if (rank == 0) mbar_arrive(ready_bar(stage));
+                    else mbar_arrive_cluster(ready_bar(stage), 0);
+                    if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (CTA 0)
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t fmt = MODE == kLeaf3xTF32P ? 2u : (MODE == kLeafBF16x3P ? 1u : 0u);
+            constexpr uint32_t idesc = make_idesc(fmt, 256, 256);
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (long long t = pair; t < total && ok; t += npairs) {
+                int g, b, tm, tn;
+                decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+                const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
+                if (!mbar_wait_cluster(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * 256);
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait_cluster(ready_bar(stage), phase, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
+                    const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                        const uint64_t ahd = sdesc_kmajor_sw64(ah + kk * 32);
+                        const uint64_t bhd = sdesc_kmajor_sw64(bh + kk * 32);
+                        const uint64_t ald = sdesc_kmajor_sw64(al + kk * 32);
+                        const uint64_t bld = sdesc_kmajor_sw64(bl + kk * 32);
+                        if constexpr (MODE == kLeaf3xTF32P) {
+                            mma_tf32_pair(d, ald, bhd, idesc, first);  // lo_a * hi_b
+                            mma_tf32_pair(d, ahd, bld, idesc, 1u);     // hi_a * lo_b
+                            mma_tf32_pair(d, ahd, bhd, idesc, 1u);     // hi_a * hi_b
+                        } else {
+                            mma_f16_pair(d, ald, bhd, idesc, first);
+                            mma_f16_pair(d, ahd, bld, idesc, 1u);
+                            mma_f16_pair(d, ahd, bhd, idesc, 1u);
+                        }
+                    }
+                    mma_commit_pair(empty_bar(stage), (uint16_t)0x3);
+                    if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit_pair(tfull_bar(acc), (uint16_t)0x3);
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------ epilogue (both CTAs)
+        const int q = warp & 3;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (long long t = pair; t < total; t += npairs) {
+            int g, b, tm, tn;
+            decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
+            const GemmGroup& G = groups[g];
+            bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int row = tm * 256 + (int)rank * Cfg::kRows + q * 32 + lane;
+            const bool row_ok = row < G.M;
+            float* crow = G.C + (long long)b * G.c_batch_stride + (long long)(row_ok ? row : 0) * G.ldc;
+            float alpha = G.alpha;
+            const float beta = G.beta;
+            if (MODE == kLeafFP16x3P && G.scale) alpha = alpha / (G.scale[0] * G.scale[1]);
+#pragma unroll 1
+            for (int c = 0; c < 256 / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256 + c * 32), r);
+                tmem_ld_wait();
+                const int col0 = tn * 256 + c * 32;
+                if (row_ok && col0 < G.N) {
+                    float* cp = crow + col0;
+                    if (G.vec_ok && col0 + 32 <= G.N) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            float4 v;
+                            v.x = alpha * __uint_as_float(r[j + 0]);
+                            v.y = alpha * __uint_as_float(r[j + 1]);
+                            v.z = alpha * __uint_as_float(r[j + 2]);
+                            v.w = alpha * __uint_as_float(r[j + 3]);
+                            if (beta != 0.0f) {
+                                const float4 o = *reinterpret_cast<const float4*>(cp + j);
+                                v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
+                            }
+                            *reinterpret_cast<float4*>(cp + j) = v;
+                        }
+                    } else {
+                        const int lim = min(32, G.N - col0);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j < lim) {
+                                float v = alpha * __uint_as_float(r[j]);
+                                if (beta != 0.0f) v += beta * cp[j];
+                                cp[j] = v;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            if (rank == 0) mbar_arrive(tempty_bar(acc));
+            else mbar_arrive_cluster(tempty_bar(acc), 0);
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    __syncthreads();
+    cluster_sync();   // every pair MMA and remote arrival of both CTAs is done
+    if (warp == 2) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStream_t stream) {
+    using Cfg = PairCfg<MODE>;
+    auto kern = leaf_gemm_pair_kernel<MODE>;
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    if (args.total_tiles <= 0) return cudaSuccess;
+    const long long pairs = args.total_tiles < num_sms / 2 ? args.total_tiles : num_sms / 2;
+    kern<<<(unsigned)(2 * pairs), Cfg::kThreads, Cfg::kSmem, stream>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_gemm_pair(const GemmArgs& args, int mode, int num_sms, cudaStream_t stream) {
+    switch (mode) {
+        case kLeaf3xTF32P: return launch_pair_impl<kLeaf3xTF32P>(args, num_sms, stream);
+        case kLeafBF16x3P: return launch_pair_impl<kLeafBF16x3P>(args, num_sms, stream);
+        case kLeafFP16x3P: return launch_pair_impl<kLeafFP16x3P>(args, num_sms, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int BN, int MODE>
 static cudaError_t launch_impl(const GemmArgs& args, int num_sms, cudaStream_t stream) {
     using Cfg = LeafCfg<BN, MODE>;

@@ -298,3 +298,29 @@ def test_deep_recursion_bit_exact(fmm, prec, m, k, n, d):
     assert info["depth"] == d
     ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
     assert np.array_equal(C, ref)
+
+
+# --- leaves on CTA pairs (cta_group::2, 256 x 256 tiles) ----------------------
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("m,k,n,d", [(256, 64, 256, 0), (300, 200, 260, 0), (777, 333, 515, 0), (1100, 900, 1300, 2),
+                                     (512, 512, 512, 3), (1, 1, 1, 0)])
+def test_pair_leaves_bit_exact(fmm, prec, m, k, n, d):
+    A = I.small_int((m, k), 16000 + m + d, r=2)
+    B = I.small_int((k, n), 16100 + n + d, r=2)
+    C, info = run(fmm, A, B, depth=d, precision=prec, leaf_tile=512)
+    assert info["leaf_tile"] == 512
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(C, ref)
+
+
+def test_pair_leaves_float_and_blas(fmm):
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(1, 21), "normal")
+    C0 = I.uniform((n, n), 17)
+    for d in (0, 2):
+        C, _ = run(fmm, A, B, C0, alpha=0.5, beta=-2.0, depth=d, leaf_tile=512)
+        ref = O.gemm(0.5, A, B, -2.0, C0)
+        assert np.max(np.abs(C - ref)) / (np.abs(A).max() * np.abs(B).max() * n) <= FP32_BOUND
+        single, _ = run(fmm, A, B, C0, alpha=0.5, beta=-2.0, depth=d, leaf_tile=256)
+        assert np.max(np.abs(C - single)) / (np.abs(A).max() * np.abs(B).max() * n) <= FP32_BOUND
