@@ -214,11 +214,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                             mma_tf32(d, ahd, sdesc_kmajor_sw64(bl + kk * 32), idesc, 1u);     // hi_a * lo_b
                             mma_tf32(d, ahd, bhd, idesc, 1u);                                 // hi_a * hi_b
                         }
-                        mma_commit(empty_bar(stage));
-                        if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
-                        continue;
-                    }
-                    if constexpr (Cfg::k16) {
+                    } else if constexpr (Cfg::k16) {
                         // 16-bit hi/lo tiles, 64-byte rows: A hi | B hi | A lo | B lo (in the
                         // split buffer, or straight from TMA in the stage for pre-split planes)
                         const uint32_t ah = (Cfg::kPre ? stage0 : lo0) + stage * Cfg::kStageBytes;
@@ -234,24 +230,22 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                             mma_f16(d, ahd, sdesc_kmajor_sw64(bl + kk * 32), idesc16, 1u);     // hi_a * lo_b
                             mma_f16(d, ahd, bhd, idesc16, 1u);                                 // hi_a * hi_b
                         }
-                        mma_commit(empty_bar(stage));
-                        if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
-                        continue;
-                    }
+                    } else {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = sdesc_kmajor_sw128(sa + kk * 32);
-                        const uint64_t bd = sdesc_kmajor_sw128(sb + kk * 32);
-                        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-                        if constexpr (MODE == kLeaf3xTF32) {
-                            const uint32_t la = lo0 + stage * Cfg::kStageBytes;
-                            const uint64_t ald = sdesc_kmajor_sw128(la + kk * 32);
-                            const uint64_t bld = sdesc_kmajor_sw128(la + Cfg::kABytes + kk * 32);
-                            mma_tf32(d, ald, bd, idesc, first);  // lo_a * hi_b
-                            mma_tf32(d, ad, bld, idesc, 1u);     // hi_a * lo_b
-                            mma_tf32(d, ad, bd, idesc, 1u);      // hi_a * hi_b
-                        } else {
-                            mma_tf32(d, ad, bd, idesc, first);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = sdesc_kmajor_sw128(sa + kk * 32);
+                            const uint64_t bd = sdesc_kmajor_sw128(sb + kk * 32);
+                            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                            if constexpr (MODE == kLeaf3xTF32) {
+                                const uint32_t la = lo0 + stage * Cfg::kStageBytes;
+                                const uint64_t ald = sdesc_kmajor_sw128(la + kk * 32);
+                                const uint64_t bld = sdesc_kmajor_sw128(la + Cfg::kABytes + kk * 32);
+                                mma_tf32(d, ald, bd, idesc, first);  // lo_a * hi_b
+                                mma_tf32(d, ad, bld, idesc, 1u);     // hi_a * lo_b
+                                mma_tf32(d, ad, bd, idesc, 1u);      // hi_a * hi_b
+                            } else {
+                                mma_tf32(d, ad, bd, idesc, first);
+                            }
                         }
                     }
                     mma_commit(empty_bar(stage));
@@ -657,8 +651,32 @@ static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStrea
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
+    // persistent pairs: only as many clusters as can be resident at once (a
+    // cluster's two CTAs must share a GPC, so this can be below num_sms / 2)
+    static int max_clusters[64] = {};
+    if (dev >= 0 && dev < 64 && max_clusters[dev] == 0) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 2;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(num_sms & ~1));
+        cfg.blockDim = dim3(Cfg::kThreads);
+        cfg.dynamicSmemBytes = Cfg::kSmem;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg);
+        if (e != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = num_sms / 2;
+        }
+        max_clusters[dev] = n < num_sms / 2 ? n : num_sms / 2;
+    }
+    const long long cap = (dev >= 0 && dev < 64) ? max_clusters[dev] : num_sms / 2;
     if (args.total_tiles <= 0) return cudaSuccess;
-    const long long pairs = args.total_tiles < num_sms / 2 ? args.total_tiles : num_sms / 2;
+    const long long pairs = args.total_tiles < cap ? args.total_tiles : cap;
     kern<<<(unsigned)(2 * pairs), Cfg::kThreads, Cfg::kSmem, stream>>>(args);
     return cudaGetLastError();
 }
