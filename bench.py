@@ -511,8 +511,9 @@ def main():
     peak_tf32_sus = pk["bf16_tflops_sustained"] * TF32_OVER_BF16
     traffic = ncu_traffic(os.path.join(ROOT, "paper_1205_2927_gb300", "csrc", "leaf_gemm.cu"),
                           f"n{n}_d{depth}_bn{bn}_{args.precision}")
-    roofline = {"bound": "tensor", "kernel": "leaf_gemm_kernel (tcgen05 kind::tf32, pre-split raw/lo planes)" if args.precision == "fp32"
-                else f"leaf_gemm_kernel ({args.precision})",
+    kname = "leaf_gemm_pair_kernel (cta_group::2, 256x256 tiles)" if bn == 512 else f"leaf_gemm_kernel (128x{bn} tiles)"
+    roofline = {"bound": "tensor", "kernel": kname + (" tcgen05 kind::tf32, pre-split raw/lo planes" if args.precision == "fp32"
+                                                      else f" {args.precision}"),
                 "achieved": round(achieved, 1), "peak": round(peak_tf32, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tf32, 3), "traffic": traffic,
                 "peak_source": f"{pk_kind} bf16 burst {pk['bf16_tflops']} x nominal tf32/bf16 ratio 1.1/2.25",

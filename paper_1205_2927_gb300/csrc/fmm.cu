@@ -167,6 +167,7 @@ struct fmm_plan_s {
     int pre16 = 0;
     int split_kind = 0;
     int pair = 0;        // leaves on CTA pairs (cta_group::2), 256 x 256 tiles
+    int tile_req = 256;  // leaf tile the plan was made for (512: CTA pairs where the precision allows)
     void* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
@@ -381,6 +382,16 @@ int fixed_depth(long long M, long long N, long long K, int cutoff) {
     return d;
 }
 
+// Leaf tile when the caller leaves it open: the CTA-pair 256 x 256 tile for the
+// pre-split precisions once both output sides of every leaf reach 1024 (from
+// there on it is at least as fast as the single-CTA tile and halves the
+// per-SM operand traffic), the single-CTA 128 x 256 tile otherwise.
+int auto_tile(long long M, long long N, int depth, const fmm_options_t& o) {
+    if (o.precision == FMM_PREC_TF32) return 256;
+    const long long mn = M < N ? M : N;
+    return (mn >> depth) >= 1024 ? 512 : 256;
+}
+
 // Leaf launch over `groups` (already filled except tile bookkeeping).
 fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int mode = -1) {
     const bool pair = p->pair && mode < 0;   // the peel border (explicit mode) stays single-CTA
@@ -396,7 +407,7 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int 
             if (mode == kLeafFP16x3P) G.scale = p->fp16_scale();
         }
         args.total_tiles = t;
-        args.raster_m = 8;
+        args.raster_m = 16;
         args.ext_maps = nullptr;
         args.ext_groups = nullptr;
         args.status = p->status;
@@ -976,6 +987,7 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
         if (M / g == 0 || N / g == 0 || K / g == 0) t.depth = 0;  // no even core: classical leaf
     }
     t.bn = bn;
+    t.tile_req = bn;
     t.mode = leaf_mode(o.precision);
     t.pre16 = 0;
     t.pair = 0;
@@ -1009,8 +1021,10 @@ int candidates(long long M, long long N, long long K, const fmm_options_t& o, Ca
     for (int d = 0; d <= 4; ++d) {
         if (d > 0 && (mn >> d) < 128) break;
         if (o.depth >= 0 && d != o.depth) continue;
-        for (int bn : {128, 256}) {
+        for (int bn : {128, 256, 512}) {
             if (o.leaf_tile && bn != o.leaf_tile) continue;
+            // CTA-pair tiles: pre-split precisions, leaves of at least one pair tile
+            if (bn == 512 && (o.precision == FMM_PREC_TF32 || (std::min(M, N) >> d) < 256)) continue;
             out[n++] = Cand{d, bn};
         }
     }
@@ -1043,8 +1057,7 @@ void raw_features(long long M, long long N, long long K, int depth, int bn, int 
 void make_child(const fmm_plan_s* p, fmm_plan_s& c) {
     fmm_options_t o = p->opt;
     o.host_operands = 0;
-    make_tmp(c, p->hm, p->hn, p->hk, p->hk, p->hn, p->hn, o, p->depth > 0 ? p->depth - 1 : 0,
-             p->opt.leaf_tile == 512 ? 512 : p->bn);
+    make_tmp(c, p->hm, p->hn, p->hk, p->hk, p->hn, p->hn, o, p->depth > 0 ? p->depth - 1 : 0, p->tile_req);
 }
 
 // Host-resident multiply.  The root level runs depth-first over the seven
@@ -1240,7 +1253,7 @@ fmm_status_t plan_choose(long long M, long long N, long long K, long long lda, l
                          cudaStream_t stream, bool query) {
     if (o.planner == FMM_PLANNER_FIXED || M == 0 || N == 0 || K == 0) {
         depth = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
-        bn = o.leaf_tile ? o.leaf_tile : 256;
+        bn = o.leaf_tile ? o.leaf_tile : auto_tile(M, N, depth, o);
         *need = plan_bytes(M, N, K, lda, ldb, ldc, o, depth, bn);
         return FMM_OK;
     }
@@ -1632,7 +1645,7 @@ fmm_status_t fmm_get_device_status(fmm_plan_t p) {
 fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precision, int* odd, int* algo) {
     if (!p) return FMM_ERR_INVALID_ARG;
     if (depth) *depth = p->depth;
-    if (leaf_tile) *leaf_tile = p->pair ? 512 : p->bn;
+    if (leaf_tile) *leaf_tile = (p->pair || (p->host && p->tile_req == 512 && p->opt.precision != FMM_PREC_TF32)) ? 512 : p->bn;
     if (precision) *precision = (int)p->opt.precision;
     if (odd) *odd = (int)p->opt.odd;
     if (algo) *algo = (int)p->opt.algo;

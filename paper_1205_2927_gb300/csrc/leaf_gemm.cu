@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            long long issued = 0;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
@@ -172,9 +173,11 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                         tma_load_3d(sa, ma, full_bar(stage), kb * Cfg::kKB, tm * kBM, b + G.a_batch_off);
                         tma_load_3d(sa + Cfg::kABytes, mb, full_bar(stage), kb * Cfg::kKB, tn * BN, b + G.b_batch_off);
                     }
+                    ++issued;
                     if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
                 }
             }
+            if (!ok || *abort_flag) drain_fills(full_bar(0), stage, phase, issued, Cfg::kStages);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
@@ -404,12 +407,14 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
 // halves, and each CTA's tensor memory holds its 128 rows of the accumulator.
 // Per SM this halves the B-operand shared-memory traffic of the single-CTA
 // kernel (operand reads + TMA writes 80 KB instead of 120 KB per K step).
-//   both CTAs  warp 0: TMA producer into local stages (local full barriers)
+//   both CTAs  warp 0: TMA producer into local stages; the copies of both CTAs
+//                      complete on CTA 0's full barrier (the cta_group::2 form of
+//                      the tensor copy), which CTA 0 arms with the bytes of both
 //              warp 2: TMEM allocation, collective over the pair
-//              warp 3: forwards "stage landed" to CTA 0's ready barrier
-//              warps 4-7: epilogue of the local 128 rows; each thread then
-//                         arrives on CTA 0's accumulator-free barrier
-//   CTA 0      warp 1: MMA issuer; commits are multicast to both CTAs
+//              warps 4-7: epilogue of the local 128 rows; each warp then
+//                         arrives once on CTA 0's accumulator-free barrier
+//   CTA 0      warp 1: MMA issuer; commits are multicast to both CTAs, so each
+//              CTA's producer waits on its own empty barrier
 template <int MODE>
 struct PairCfg {
     static constexpr int kRows = 128;                          // rows per CTA of A and of B^T
@@ -420,7 +425,7 @@ struct PairCfg {
     static constexpr int kBarBytes = 256;
     static constexpr int kThreads = 256;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kBarBytes;
-    static_assert((3 * kStages + 4) * 8 + 16 <= kBarBytes, "barrier area");
+    static_assert((2 * kStages + 4) * 8 + 16 <= kBarBytes, "barrier area");
     static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
@@ -435,13 +440,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     const uint32_t stage0 = base;
     const uint32_t bar0 = base + Cfg::kStages * Cfg::kStageBytes;
     uint8_t* bar_ptr = base_ptr + (bar0 - base);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 8 * (3 * Cfg::kStages + 4));
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar_ptr + 8 * (3 * Cfg::kStages + 4) + 8);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_ptr + 8 * (2 * Cfg::kStages + 4));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar_ptr + 8 * (2 * Cfg::kStages + 4) + 8);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (Cfg::kStages + s); };
-    auto ready_bar = [&](int s) { return bar0 + 8u * (2 * Cfg::kStages + s); };
-    auto tfull_bar = [&](int a) { return bar0 + 8u * (3 * Cfg::kStages + a); };
-    auto tempty_bar = [&](int a) { return bar0 + 8u * (3 * Cfg::kStages + 2 + a); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * Cfg::kStages + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * Cfg::kStages + 2 + a); };
 
     const uint32_t rank = cluster_ctarank();
     const int warp = threadIdx.x >> 5;
@@ -455,13 +459,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::kStages; ++s) {
-            mbar_init(full_bar(s), 1);
+            mbar_init(full_bar(s), 1);     // CTA 0's arming arrival (used in CTA 0)
             mbar_init(empty_bar(s), 1);
-            mbar_init(ready_bar(s), 2);    // one forwarded arrival per CTA (used in CTA 0)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull_bar(a), 1);
-            mbar_init(tempty_bar(a), 256); // every epilogue thread of both CTAs (used in CTA 0)
+            mbar_init(tempty_bar(a), 8);   // every epilogue warp of both CTAs (used in CTA 0)
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -482,6 +485,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            long long issued = 0;
             for (long long t = pair; t < total && ok; t += npairs) {
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
@@ -490,36 +494,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 const int a0 = tm * 256 + (int)rank * Cfg::kRows, b0 = tn * 256 + (int)rank * Cfg::kRows;
                 const int ab = b + G.a_batch_off, bb = b + G.b_batch_off;
                 for (int kb = 0; kb < nk; ++kb) {
+                    // the stage is free in this CTA once the MMAs that read it
+                    // completed (their commit is multicast to both CTAs)
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, status)) { ok = false; break; }
-                    mbar_arrive_expect_tx(full_bar(stage), Cfg::kStageBytes);
+                    // CTA 0 arms its full barrier with the bytes of both CTAs; a
+                    // peer copy that lands first only drives the tx-count below
+                    // zero, which the arming arrival brings back
+                    if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * Cfg::kStageBytes);
                     const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
                     const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
                     const int x = kb * Cfg::kKB;
-                    tma_load_3d(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
-                    tma_load_3d(bh, maps + G.map_b, full_bar(stage), x, b0, bb);
-                    tma_load_3d(al, maps + G.map_a_lo, full_bar(stage), x, a0, ab);
-                    tma_load_3d(bl, maps + G.map_b_lo, full_bar(stage), x, b0, bb);
+                    tma_load_3d_pair(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
+                    tma_load_3d_pair(bh, maps + G.map_b, full_bar(stage), x, b0, bb);
+                    tma_load_3d_pair(al, maps + G.map_a_lo, full_bar(stage), x, a0, ab);
+                    tma_load_3d_pair(bl, maps + G.map_b_lo, full_bar(stage), x, b0, bb);
+                    ++issued;
                     if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
                 }
             }
-        }
-    } else if (warp == 3) {
-        // ------------------------------------------------ forwarder (both CTAs)
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            bool ok = true;
-            for (long long t = pair; t < total && ok; t += npairs) {
-                int g, b, tm, tn;
-                decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
-                const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
-                for (int kb = 0; kb < nk; ++kb) {
-                    if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
-                    if (rank == 0) mbar_arrive(ready_bar(stage));
-                    else mbar_arrive_cluster(ready_bar(stage), 0);
-                    if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
-                }
-            }
+            // the copies of both CTAs complete on CTA 0's full barriers, and the
+            // closing cluster barrier holds CTA 1 until CTA 0 has drained them
+            if (rank == 0 && (!ok || *abort_flag)) drain_fills(full_bar(0), stage, phase, issued, Cfg::kStages);
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (CTA 0)
@@ -539,7 +534,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 256);
                 for (int kb = 0; kb < nk; ++kb) {
-                    if (!mbar_wait_cluster(ready_bar(stage), phase, abort_flag, status)) { ok = false; break; }
+                    // both CTAs' copies complete on this CTA's barrier (complete_tx of
+                    // the async proxy, read by the async proxy): a CTA-scope acquire
+                    // suffices, and avoids a cluster-scope fence per stage
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
                     const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
@@ -622,9 +620,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                     }
                 }
             }
+            // every lane's tensor-memory reads are complete (wait::ld above);
+            // one arrival per warp releases the accumulator to CTA 0's MMAs
             tc_fence_before();
-            if (rank == 0) mbar_arrive(tempty_bar(acc));
-            else mbar_arrive_cluster(tempty_bar(acc), 0);
+            __syncwarp();
+            if (lane == 0) {
+                if (rank == 0) mbar_arrive(tempty_bar(acc));
+                else mbar_arrive_cluster(tempty_bar(acc), 0);
+            }
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }

@@ -71,6 +71,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Abort path of a TMA producer: waits (time-limited, whatever the abort flag)
+// for the last min(issued, stages) stage fills to land, so that no bulk copy is
+// still writing shared memory when the CTA exits.  (stage, phase) is the next
+// fill position; full barrier s sits at full0 + 8 s.
+__device__ __forceinline__ void drain_fills(uint32_t full0, int stage, uint32_t phase, long long issued,
+                                            int stages) {
+    const unsigned long long t0 = global_ns();
+    for (long long j = 0; j < issued && j < stages; ++j) {
+        if (--stage < 0) { stage = stages - 1; phase ^= 1u; }
+        while (!mbar_try_wait(full0 + 8u * (uint32_t)stage, phase))
+            if (global_ns() - t0 > FMM_WAIT_LIMIT_NS) return;
+    }
+}
+
 // ---------------------------------------------------------------- TMA
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -176,6 +190,27 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
             }
         }
     }
+}
+// expect_tx arrival on the mbarrier at local address `bar` of cluster CTA `rank`.
+__device__ __forceinline__ void mbar_arrive_expect_tx_cluster(uint32_t bar, uint32_t rank, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b32 ra;\n\t"
+        "mapa.shared::cluster.u32 ra, %0, %1;\n\t"
+        "mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [ra], %2;\n\t}" ::"r"(bar),
+        "r"(rank), "r"(bytes)
+        : "memory");
+}
+// TMA tile load into this CTA's shared memory whose completion is signalled on
+// the mbarrier at local address `bar` of cluster CTA 0 (the pair's MMA issuer).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                                 int c2) {
+    asm volatile(
+        "{\n\t.reg .b32 rb;\n\t"
+        "mapa.shared::cluster.u32 rb, %5, 0;\n\t"
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [rb];\n\t}" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
 }
 // Tensor memory of a CTA pair: allocated / released collectively by one warp of each CTA.
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {

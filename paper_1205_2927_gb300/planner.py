@@ -1,7 +1,7 @@
 """Learned planner pipeline: timings -> cost-model training on the GPU -> plan choice.
 
 1. ``collect``: for each shape, every candidate plan (depth 0..4 x leaf tile
-   {128, 256}) is timed on the device by the library's exhaustive autotuner
+   {128, 256, 512}) is timed on the device by the library's exhaustive autotuner
    (``fmm_autotune``); each (shape, candidate, milliseconds) is one record.
 2. ``train``: the 6-64-64-1 network predicts log(ms) from the standardised
    features; it is trained with the library's own forward/backward/Adam
