@@ -37,7 +37,7 @@ TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tensor-rate ratio, GB300
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fmm", choices=["fmm", "reference"])
     ap.add_argument("--n", type=int, default=16384)
@@ -78,27 +78,47 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []          # (host time, csv line) per sample
+        self.window = None       # host-time bounds of the timed region
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
 
     def start(self):
+        """Start sampling and wait (up to 5 s) for the first sample, so that the
+        sampler is running before the timed region begins."""
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.02)
 
     def stop(self):
         if not self.proc:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            out = ""
+        self.reader.join(timeout=5)
+        lines, where = self.lines, "whole run"
+        if self.window:
+            inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1]]
+            if inside:
+                lines, where = inside, "timed region"
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for _, line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -113,6 +133,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "samples_in": where,
                 "reasons": sorted(reasons)}
 
 
@@ -401,7 +422,33 @@ def wl_planner(args):
 WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "split": wl_split, "batched": wl_batched,
              "planner": wl_planner}
 
-def timed(torch, dist, world, fn, steps, warmup):
+def cublas_tf32_tflops(torch, n=8192, reps=10):
+    """TF32 tensor-core rate of the vendor library on this GPU (a live
+    microbenchmark: torch.matmul with TF32 allowed, n^3, median of reps)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.rand(n, n, device="cuda")
+        b = torch.rand(n, n, device="cuda")
+        c = torch.empty(n, n, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            torch.matmul(a, b, out=c)
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        del a, b, c
+        return 2.0 * n ** 3 / (statistics.median(ts) * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def timed(torch, dist, world, fn, steps, warmup, clocks=None):
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
@@ -409,11 +456,14 @@ def timed(torch, dist, world, fn, steps, warmup):
         dist.barrier()
     torch.cuda.synchronize()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
     s.record()
     for _ in range(steps):
         fn()
     e.record()
     torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.window = (t0, time.perf_counter())
     if world > 1:
         dist.barrier()
     ms = s.elapsed_time(e) / steps
@@ -464,8 +514,9 @@ def main():
         step()
     torch.cuda.synchronize()
     wplan.profile(True)  # reset: count only the timed steps
-    ms = timed(torch, dist, world, step, args.steps, 0)
+    ms = timed(torch, dist, world, step, args.steps, 0, clocks)
     clk = clocks.stop()
+    phase_bytes = wplan.phase_bytes()
     prof = wplan.profile_read()
     wplan.profile(False)
     assert wplan.device_status() == 0, "device status word set"
@@ -520,8 +571,22 @@ def main():
                 "frac_of_sustained": round(achieved / peak_tf32_sus, 3),
                 "work": f"{tc_products} TF32 products x 2*{leaf_count}*{leaf_dim}^3 flops per launch",
                 "leaf_ms_per_launch": round(leaf_ms, 3)}
+    if args.precision in ("fp32", "tf32"):
+        tf32 = cublas_tf32_tflops(torch)
+        roofline["cublas_tf32_tflops"] = round(tf32, 1)
+        roofline["frac_of_cublas_tf32"] = round(achieved / tf32, 3)
     phases = {"pre_add_ms": round(prof["pre_ms"] / max(prof["calls"], 1), 3), "leaf_ms": round(leaf_ms, 3),
               "post_add_ms": round(prof["post_ms"] / max(prof["calls"], 1), 3)}
+    # the addition passes are HBM-bound: algorithmic bytes per call / phase time
+    # against the measured copy bandwidth
+    additions = {}
+    for key, bkey, tkey in (("pre", "pre_bytes", "pre_add_ms"), ("post", "post_bytes", "post_add_ms")):
+        b, t = phase_bytes[bkey], phases[tkey]
+        if b > 0 and t > 0:
+            gbs = b / (t * 1e-3) / 1e9
+            additions[key] = {"bytes": int(b), "ms": t, "achieved_gbs": round(gbs, 1), "peak_gbs": pk["hbm_gbs"],
+                              "frac": round(gbs / pk["hbm_gbs"], 3)}
+    additions["peak_source"] = f"{pk_kind} HBM copy bandwidth"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -541,6 +606,7 @@ def main():
         "classical": classical,
         "speedup_vs_classical": round(value / classical["gflops"], 3) if classical else None,
         "phases": phases,
+        "additions": additions,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

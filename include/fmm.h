@@ -173,6 +173,17 @@ const char* fmm_last_error(void);
  * is cleared by the read. */
 fmm_status_t fmm_get_device_status(fmm_plan_t plan);
 
+/* Algorithmic bytes of the plan's last call (device-operand plans; 0 for
+ * host-resident ones): every read and write the addition passes need, counted
+ * once, without cache or padding effects.  pre_bytes covers the passes before
+ * the leaf launch (FP16X3 operand scales, operand splits into hi / lo planes,
+ * transposes, the S / T pre-additions of the Winograd recursion); post_bytes
+ * the passes after it (the U post-additions, alpha / beta into C, and for peeled
+ * plans the border's operand copies).  Dividing by the phase times of
+ * fmm_plan_profile_read gives the addition kernels' achieved HBM bandwidth.
+ * Either pointer may be NULL. */
+fmm_status_t fmm_plan_phase_bytes(fmm_plan_t plan, double* pre_bytes, double* post_bytes);
+
 /* Plan inspection: depth, leaf tile width, precision and odd mode the plan
  * uses (after the planner ran); any pointer may be NULL. */
 fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* precision,

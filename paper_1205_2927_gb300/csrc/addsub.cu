@@ -591,6 +591,72 @@ __global__ void __launch_bounds__(128) pre_add2_kernel(View P, long long h, long
     }
 }
 
+// Root B side of a depth-2 plan in one pass, straight from the caller's
+// row-major B (valid K x N, zero outside) into the 49 leaf operands of B^T,
+// split into planes.  Leaf position (n, k) of B^T sub-block (a, b) is
+// B[b * w + k][a * h + n] (h = N0 / 4, w = K0 / 4).  A 32 (k) x 32 (n) block of
+// positions is loaded coalesced along n; each thread keeps 4 rows (k) packed in
+// the lanes of a float4, so the chain is pre_add2_kernel's, element for
+// element.  Grandchildren leave through a shared tile, transposed, 7 at a time.
+template <int KIND>
+__global__ void __launch_bounds__(256) pre_add2_b_root_kernel(const float* __restrict__ B, long long ldb, long long K,
+                                                              long long N, long long h, long long w, Stack16 out,
+                                                              const float* __restrict__ scale) {
+    __shared__ float tile[7][32][33];
+    const float sc = scale ? scale[1] : 1.0f;
+    const long long k0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long n = n0 + tx;
+    float4 X[4][4];   // X[a][b]: sub-block (a, b) of B^T; lane l = row k0 + ty + 8 l
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float t[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const long long k = k0 + ty + 8 * l;
+                const long long row = b * w + k, col = a * h + n;
+                t[l] = (k < w && n < h && row < K && col < N) ? __ldg(B + row * ldb + col) : 0.0f;
+            }
+            X[a][b] = f4(t[0], t[1], t[2], t[3]);
+        }
+    const int t = ty * 32 + tx;
+    const int nl = t >> 3, kq = (t & 7) * 4;   // store role: 4 consecutive k of row n0 + nl
+    const long long on = n0 + nl, ok = k0 + kq;
+    const bool store = on < h && ok < w;
+#pragma unroll 1
+    for (int i = 0; i < 7; ++i) {
+        float4 Ci[4];   // child i's quadrant t
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 Qt[4] = {X[(q >> 1)][(q & 1)], X[(q >> 1)][2 + (q & 1)], X[2 + (q >> 1)][(q & 1)],
+                                  X[2 + (q >> 1)][2 + (q & 1)]};
+            float4 ch[7];
+            children7<1>(Qt, ch);
+            Ci[q] = ch[i];
+        }
+        float4 g[7];
+        children7<1>(Ci, g);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            tile[j][ty][tx] = g[j].x;
+            tile[j][ty + 8][tx] = g[j].y;
+            tile[j][ty + 16][tx] = g[j].z;
+            tile[j][ty + 24][tx] = g[j].w;
+        }
+        __syncthreads();
+        if (store) {
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                const float4 v = make_float4(tile[j][kq][nl], tile[j][kq + 1][nl], tile[j][kq + 2][nl], tile[j][kq + 3][nl]);
+                split_store<KIND>(out.hi, out.lo, (i * 7 + j) * out.child_stride + on * out.ld + ok, v, sc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Post-additions of two consecutive levels in one pass: for each node, its 49
 // grandchild products P[(node * 7 + i) * 7 + j] (h x w, row stride ld_in) ->
 // the node output (4h x 4w).  The children's quadrant values are formed with
@@ -858,6 +924,20 @@ cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& ou
     else     { if (side_b) { FMM_PRE2K(false, 1) } else { FMM_PRE2K(false, 0) } }
 #undef FMM_PRE2K
 #undef FMM_PRE2
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add2_b_root(const float* B, long long ldb, long long K, long long N, long long h, long long w,
+                                   const Stack16& out, int kind, const float* scale, cudaStream_t stream) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    if (w % 4) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((h + 31) / 32), (unsigned)((w + 31) / 32));
+    dim3 block(32, 8);
+    switch (kind) {
+        case kSplitBF16: pre_add2_b_root_kernel<kSplitBF16><<<grid, block, 0, stream>>>(B, ldb, K, N, h, w, out, scale); break;
+        case kSplitFP16: pre_add2_b_root_kernel<kSplitFP16><<<grid, block, 0, stream>>>(B, ldb, K, N, h, w, out, scale); break;
+        default: pre_add2_b_root_kernel<kSplitTF32><<<grid, block, 0, stream>>>(B, ldb, K, N, h, w, out, scale); break;
+    }
     return cudaGetLastError();
 }
 

@@ -179,7 +179,9 @@ struct fmm_plan_s {
     // depth 2: both levels at once from / into the caller's matrices
     bool fuse_root_pre() const { return pre16 && depth == 2; }
     bool fuse_root_post() const { return depth == 2; }
-    float* bt_root = nullptr;   // root-fused plans: B^T zero-padded to N0 x K0
+    // algorithmic bytes (reads + writes the passes need) of the last call's
+    // addition phases: [0] before the leaf launch, [1] after it
+    double acct[2] = {0.0, 0.0};
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -300,10 +302,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             L.full = (l < d - 1 || l == 0 || p->pre16) ? 1 : 0;
             const long long per = L.full ? 7 : 4;
             if (p->fuse_pre() && l == d - 2) continue;   // written by neither pass: fused away
-            if (p->fuse_root_pre() && l == 0) {           // fused away; B^T of the root instead
-                p->bt_root = cv.take<float>((size_t)(p->N0 * p->K0));
-                continue;
-            }
+            if (p->fuse_root_pre() && l == 0) continue;   // fused away (both sides read the caller's operands)
             if (p->pre16 && l == d - 1) {   // the leaves' operands, as split planes
                 p->ld16 = rup(C.k, 128 / (long long)p->es16());   // 128-byte row pitch
                 for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
@@ -446,6 +445,7 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
         FMM_CUDA(launch_split16(A, p->lda, p->M, p->K, sa, 0, bf, scale, 0, stream));
         FMM_CUDA(launch_split16(B, p->ldb, p->K, p->N, sb, 1, bf, scale, 1, stream));
         p->launches += 2;
+        p->acct[0] += (double)(p->M * p->K + p->K * p->N) * (4.0 + 2.0 * p->es16());
         mark(p, 1, stream);
         GemmArgs args;
         memset(&args, 0, sizeof(args));
@@ -468,11 +468,13 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
     }
     FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
     p->launches += 1;
+    p->acct[0] += 8.0 * (double)(p->K * p->N);
     const float* Aop = A;
     long long lda = p->lda;
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
         FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
         p->launches += 1;
+        p->acct[0] += 8.0 * (double)(p->M * p->K);
         Aop = p->Acopy;
         lda = p->ld_acopy;
     }
@@ -503,11 +505,13 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
 fmm_status_t run_border(fmm_plan_s* p, float alpha, const float* A, const float* B, float* C, cudaStream_t stream) {
     FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
     p->launches += 1;
+    p->acct[1] += 8.0 * (double)(p->K * p->N);
     const float* Aop = A;
     long long lda = p->lda;
     if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
         FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
         p->launches += 1;
+        p->acct[1] += 8.0 * (double)(p->M * p->K);
         Aop = p->Acopy;
         lda = p->ld_acopy;
     }
@@ -552,18 +556,19 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
     Level* lv = p->lv;
     const int kind = p->split_kind;
     const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
+    const double pl = 2.0 * (double)p->es16();   // bytes per element of a hi + lo plane pair
+    const double root_in = 4.0 * (double)(p->Mw * p->Kw + p->Kw * p->Nw);
     if (p->fuse_root_pre()) {
-        // both levels at once: root -> the 49 leaf operands; B goes through one
-        // zero-padded transposed copy so that both sides are K-major
+        // both levels at once: root -> the 49 leaf operands; the B side reads the
+        // caller's row-major B and writes the K-major (transposed) leaf planes
         const Level& Lf = lv[2];
-        FMM_CUDA(launch_transpose(B, p->ldb, p->Kw, p->Nw, p->bt_root, p->K0, stream, p->N0, p->K0));
         View va{A, p->lda, 0, p->M0, p->K0, p->Mw, p->Kw};
-        View vb{p->bt_root, p->K0, 0, p->N0, p->K0, p->N0, p->K0};
         Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 49};
         Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 49};
         FMM_CUDA(launch_pre_add2(va, 1, sa, 0, kind, scale, stream));
-        FMM_CUDA(launch_pre_add2(vb, 1, sb, 1, kind, scale, stream));
-        p->launches += 3;
+        FMM_CUDA(launch_pre_add2_b_root(B, p->ldb, p->Kw, p->Nw, Lf.n, Lf.k, sb, kind, scale, stream));
+        p->launches += 2;
+        p->acct[0] += root_in + 49.0 * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
         return FMM_OK;
     }
     {
@@ -574,11 +579,13 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
             Stack16 sb{p->b16[0], p->b16[1], p->ld16, C1.n * p->ld16, 7};
             FMM_CUDA(launch_pre_add16(va, 1, sa, 0, kind, scale, stream));
             FMM_CUDA(launch_pre_add16_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, kind, scale, stream));
+            p->acct[0] += root_in + 7.0 * (double)(C1.m * C1.k + C1.n * C1.k) * pl;
         } else {
             Stack sa{lv[0].achild, C1.k, C1.m * C1.k, 7};
             FMM_CUDA(launch_pre_add(va, 1, sa, 0, 1, stream));
             Stack sb{lv[0].bchild, C1.k, C1.n * C1.k, 7};
             FMM_CUDA(launch_pre_add_b_root(B, p->ldb, p->Kw, p->Nw, C1.k, C1.n, sb, 1, stream));
+            p->acct[0] += root_in + 7.0 * (double)(C1.m * C1.k + C1.n * C1.k) * 4.0;
         }
         p->launches += 2;
     }
@@ -588,6 +595,7 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         const Level& Pa = lv[l - 1];
         View va{Pa.achild, L.k, L.m * L.k, L.m, L.k, L.m, L.k};
         View vb{Pa.bchild, L.k, L.n * L.k, L.n, L.k, L.n, L.k};
+        const double in = 4.0 * (double)L.nodes * (double)(L.m * L.k + L.n * L.k);
         if (p->fuse_pre() && l == d - 2) {
             // levels d-2 and d-1 at once: level-(d-2) node operands -> the leaf operands
             const Level& Lf = lv[d];
@@ -596,6 +604,7 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
             FMM_CUDA(launch_pre_add2(va, L.nodes, sa, 0, kind, scale, stream));
             FMM_CUDA(launch_pre_add2(vb, L.nodes, sb, 1, kind, scale, stream));
             p->launches += 2;
+            p->acct[0] += in + 49.0 * (double)L.nodes * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
             break;
         }
         if (p->pre16 && l == d - 1) {
@@ -604,6 +613,7 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
             FMM_CUDA(launch_pre_add16(va, L.nodes, sa, 0, kind, scale, stream));
             FMM_CUDA(launch_pre_add16(vb, L.nodes, sb, 1, kind, scale, stream));
             p->launches += 2;
+            p->acct[0] += in + 7.0 * (double)L.nodes * (double)(Ch.m * Ch.k + Ch.n * Ch.k) * pl;
             continue;
         }
         const int per = L.full ? 7 : 4;
@@ -612,6 +622,7 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         FMM_CUDA(launch_pre_add(va, L.nodes, sa, 0, L.full, stream));
         FMM_CUDA(launch_pre_add(vb, L.nodes, sb, 1, L.full, stream));
         p->launches += 2;
+        p->acct[0] += in + (double)per * (double)L.nodes * (double)(Ch.m * Ch.k + Ch.n * Ch.k) * 4.0;
     }
     return FMM_OK;
 }
@@ -698,12 +709,14 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
     const int d = p->depth;
     Level* lv = p->lv;
     int top = d - 1;
+    const double root_out = 4.0 * (double)(p->Mw * p->Nw) * (beta != 0.0f ? 2.0 : 1.0);
     if (p->fuse_root_post()) {
         // both levels at once: leaf products -> the caller's C (alpha, beta, valid window)
         const Level& Lf = lv[2];
         FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, 1, Lf.m, Lf.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
                                   stream));
         p->launches += 1;
+        p->acct[1] += 49.0 * 4.0 * (double)(Lf.m * Lf.n) + root_out;
         return FMM_OK;
     }
     if (p->fuse_post()) {
@@ -713,6 +726,7 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
         FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, L.nodes, Lf.m, Lf.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
                                   0.f, stream));
         p->launches += 1;
+        p->acct[1] += 4.0 * (double)L.nodes * (49.0 * (double)(Lf.m * Lf.n) + (double)(L.m * L.n));
         top = d - 3;
     }
     for (int l = top; l >= 0; --l) {
@@ -722,9 +736,11 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
         if (l > 0) {
             FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, L.nodes, Ch.m, Ch.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
                                      0.f, stream));
+            p->acct[1] += 4.0 * (double)L.nodes * (7.0 * (double)(Ch.m * Ch.n) + (double)(L.m * L.n));
         } else {
             FMM_CUDA(launch_post_add(in, Ch.n, Ch.m * Ch.n, 1, Ch.m, Ch.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
                                      stream));
+            p->acct[1] += 4.0 * 7.0 * (double)(Ch.m * Ch.n) + root_out;
         }
         p->launches += 1;
     }
@@ -754,12 +770,14 @@ fmm_status_t run_winograd(fmm_plan_s* p, float alpha, const float* A, const floa
 // One multiply with the plan's schedule (FP16x3 first derives its operand scales).
 fmm_status_t execute(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                      cudaStream_t stream) {
+    p->acct[0] = p->acct[1] = 0.0;
     if (p->mode == kLeafFP16x3 || p->mode == kLeafFP16x3P) {
         // operand magnitudes of the leaves are bounded by 4^depth times the root's
         const float bound = (float)(1LL << (2 * p->depth));
         FMM_CUDA(launch_fp16_scales(A, p->lda, p->M, p->K, B, p->ldb, p->N, bound, p->fp16_scale(),
                                     p->fp16_scratch(), stream));
         p->launches += 3;
+        p->acct[0] += 4.0 * (double)(p->M * p->K + p->K * p->N);
     }
     return (p->depth == 0) ? run_classical(p, alpha, A, B, beta, C, stream)
                            : run_winograd(p, alpha, A, B, beta, C, stream);
@@ -1588,6 +1606,14 @@ fmm_status_t fmm_plan_profile(fmm_plan_t p, int enable) {
     p->launches = 0;
     p->calls = 0;
     return s;
+}
+
+fmm_status_t fmm_plan_phase_bytes(fmm_plan_t p, double* pre_bytes, double* post_bytes) {
+    if (!p) return FMM_ERR_INVALID_ARG;
+    // host-resident plans stream quadrants through a child plan: not reported
+    if (pre_bytes) *pre_bytes = p->host ? 0.0 : p->acct[0];
+    if (post_bytes) *post_bytes = p->host ? 0.0 : p->acct[1];
+    return FMM_OK;
 }
 
 fmm_status_t fmm_plan_profile_read(fmm_plan_t p, double* pre_ms, double* leaf_ms, double* post_ms,

@@ -189,6 +189,10 @@ cudaError_t launch_split16(const float* X, long long ldx, long long rows, long l
 // C <- alpha * U + beta * C inside valid_rows x valid_cols.
 cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& out, int side_b, int kind,
                             const float* scale, cudaStream_t stream);
+// Root B side of a depth-2 plan: the caller's row-major B (K x N valid) straight
+// into the 49 leaf operands of B^T (h = N0 / 4 rows, w = K0 / 4 columns each).
+cudaError_t launch_pre_add2_b_root(const float* B, long long ldb, long long K, long long N, long long h, long long w,
+                                   const Stack16& out, int kind, const float* scale, cudaStream_t stream);
 cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
                              long long w, float* out, long long ld_out, long long out_node_stride,
                              long long valid_rows, long long valid_cols, float alpha, float beta,

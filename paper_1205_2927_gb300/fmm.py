@@ -76,6 +76,8 @@ def _load():
     lib.fmm_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), C.POINTER(i64), C.POINTER(i64)]
     lib.fmm_plan_profile_read.restype = C.c_int
+    lib.fmm_plan_phase_bytes.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.fmm_plan_phase_bytes.restype = C.c_int
     return lib
 
 
@@ -156,6 +158,12 @@ def fmm_plan_profile_read(plan):
     return dict(pre_ms=v[0].value, leaf_ms=v[1].value, post_ms=v[2].value, launches=v[3].value, calls=v[4].value)
 
 
+def fmm_plan_phase_bytes(plan):
+    pre, post = C.c_double(), C.c_double()
+    _check(_lib.fmm_plan_phase_bytes(plan, C.byref(pre), C.byref(post)), "fmm_plan_phase_bytes")
+    return dict(pre_bytes=pre.value, post_bytes=post.value)
+
+
 # ------------------------------------------------------------------ convenience over torch tensors
 
 class Plan:
@@ -196,6 +204,10 @@ class Plan:
 
     def profile_read(self):
         return fmm_plan_profile_read(self.handle)
+
+    def phase_bytes(self):
+        """Algorithmic bytes of the last call's addition phases (pre_bytes, post_bytes)."""
+        return fmm_plan_phase_bytes(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -90,6 +90,7 @@ def test_invalid_options_rejected(F):
 def test_gemm_rejects_null_plan(F):
     assert F.library().fmm_gemm(None, C.c_float(1), None, None, C.c_float(0), None, None) == 1
     F.library().fmm_free(None)  # NULL-safe
+    assert F.library().fmm_plan_phase_bytes(None, None, None) == 1
 
 
 def test_no_cpu_fallback_without_gpu(F):

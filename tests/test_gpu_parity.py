@@ -324,3 +324,35 @@ def test_pair_leaves_float_and_blas(fmm):
         assert np.max(np.abs(C - ref)) / (np.abs(A).max() * np.abs(B).max() * n) <= FP32_BOUND
         single, _ = run(fmm, A, B, C0, alpha=0.5, beta=-2.0, depth=d, leaf_tile=256)
         assert np.max(np.abs(C - single)) / (np.abs(A).max() * np.abs(B).max() * n) <= FP32_BOUND
+
+
+# --- algorithmic bytes of the addition phases -----------------------------------
+
+def test_phase_bytes_closed_forms(fmm):
+    import torch
+    n = 1024
+    A = torch.rand(n, n, device="cuda")
+    B = torch.rand(n, n, device="cuda")
+    C = torch.empty(n, n, device="cuda")
+    # depth 0 (FP32): the operands are read once and written as raw + lo planes
+    p = fmm.Plan(n, n, n, depth=0)
+    p(A, B, C)
+    torch.cuda.synchronize()
+    assert p.phase_bytes() == {"pre_bytes": 2 * n * n * (4 + 8), "post_bytes": 0}
+    p.close()
+    # depth 2: root in, 49 leaf operands per side out (raw + lo fp32 planes);
+    # 49 leaf products in, C out (read too when beta != 0)
+    h = n // 4
+    for beta, c_passes in ((0.0, 1), (0.5, 2)):
+        p = fmm.Plan(n, n, n, depth=2)
+        p(A, B, C, beta=beta)
+        torch.cuda.synchronize()
+        assert p.phase_bytes() == {"pre_bytes": 2 * n * n * 4 + 2 * 49 * h * h * 8,
+                                   "post_bytes": 49 * h * h * 4 + c_passes * n * n * 4}
+        p.close()
+    # BF16X3 planes are 2 + 2 bytes per element
+    p = fmm.Plan(n, n, n, depth=2, precision="bf16x3")
+    p(A, B, C)
+    torch.cuda.synchronize()
+    assert p.phase_bytes()["pre_bytes"] == 2 * n * n * 4 + 2 * 49 * h * h * 4
+    p.close()
