@@ -252,7 +252,7 @@ def wl_single1024(args):
     for d in (0, 2):
         p = fmm.Plan(n, n, n, depth=d)
         ms = event_ms(torch, lambda: p(dA, dB, dC), 20, 5)
-        emit(args, {"workload": "single_n1024", "depth": d, "ms": round(ms, 4),
+        emit(args, {"workload": "single_n1024", "depth": d, "leaf_tile": p.info["leaf_tile"], "ms": round(ms, 4),
                     "gflops": round(2 * n ** 3 / ms / 1e6, 1), "error": sampled_error(np, torch, dC, A_h, B_h, 64)})
         p.close()
 
@@ -275,6 +275,7 @@ def wl_sweep(args):
                     p = fmm.Plan(n, n, n, depth=d, odd=odd)
                     ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 2)
                     err = sampled_error(np, torch, dC, A_h, B_h)
+                    tile = p.info["leaf_tile"]
                     p.close()
                     wall = None
                     if odd == "pad" and dist == "uniform":
@@ -290,7 +291,7 @@ def wl_sweep(args):
                             ws.append((time.perf_counter() - t0) * 1e3)
                         wall = sorted(ws)[1]
                         hp.close()
-                    emit(args, {"workload": "sweep", "n": n, "depth": d, "odd": odd, "dist": dist,
+                    emit(args, {"workload": "sweep", "n": n, "depth": d, "leaf_tile": tile, "odd": odd, "dist": dist,
                                 "device_ms": round(ms, 3), "device_gflops": round(2 * n ** 3 / ms / 1e6, 1),
                                 "host_wallclock_ms": round(wall, 3) if wall else None,
                                 "host_gflops": round(2 * n ** 3 / wall / 1e6, 1) if wall else None,
@@ -316,9 +317,10 @@ def wl_split(args):
                     p = fmm.Plan(m, n, k, depth=d, precision=prec)
                     ms = event_ms(torch, lambda: p(dA, dB, dC), 2, 1)
                     err = sampled_error(np, torch, dC, A_h, B_h)
+                    tile = p.info["leaf_tile"]
                     p.close()
                     emit(args, {"workload": "split", "M": m, "K": k, "N": n, "dist": dist, "precision": prec,
-                                "depth": d, "ms": round(ms, 3), "gflops": round(2 * m * n * k / ms / 1e6, 1),
+                                "depth": d, "leaf_tile": tile, "ms": round(ms, 3), "gflops": round(2 * m * n * k / ms / 1e6, 1),
                                 "error": err, "finite": bool(torch.isfinite(dC).all().item())})
             del dA, dB, dC
             torch.cuda.empty_cache()
@@ -587,6 +589,14 @@ def main():
             additions[key] = {"bytes": int(b), "ms": t, "achieved_gbs": round(gbs, 1), "peak_gbs": pk["hbm_gbs"],
                               "frac": round(gbs / pk["hbm_gbs"], 3)}
     additions["peak_source"] = f"{pk_kind} HBM copy bandwidth"
+    # end-to-end bound of the schedule: leaf work at the measured TF32 rate plus
+    # the addition bytes at the measured HBM bandwidth, against the measured step
+    if roofline.get("cublas_tf32_tflops"):
+        t_star = (leaf_flops / (roofline["cublas_tf32_tflops"] * 1e12)
+                  + (phase_bytes["pre_bytes"] + phase_bytes["post_bytes"]) / (pk["hbm_gbs"] * 1e9)) * 1e3
+        additions["bound_ms"] = {"t_star": round(t_star, 3), "measured": round(ms, 3),
+                                 "t_star_over_measured": round(t_star / ms, 3),
+                                 "model": "leaf flops / cuBLAS TF32 rate + addition bytes / HBM copy bandwidth"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
