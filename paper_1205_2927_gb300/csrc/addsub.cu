@@ -345,9 +345,13 @@ __global__ void __launch_bounds__(128) quad_pre_kernel(QuadPre q) {
 }
 
 // Root post-additions of the host-streamed schedule from the seven product
-// buffers (h x w, row stride ld) into quadrant buffers of C (same layout):
-//   part 0: C11 = alpha * (P1 + P2) + beta * C11
-//   part 1: C12 = alpha * U5, C21 = alpha * U6, C22 = alpha * U7 (+ beta * old)
+// buffers (h x w, row stride ld) into one quadrant buffer of C (same layout),
+// with the U-chain's operation order, so each quadrant can be formed (and
+// copied out) as soon as its products exist:
+//   part 0: C11 = alpha * U1 + beta * C11, U1 = P1 + P2
+//   part 1: C12 = alpha * U5 + beta * C12, U5 = ((P1 + P6) + P5) + P3
+//   part 2: C21 = alpha * U6 + beta * C21, U6 = ((P1 + P6) + P7) - P4
+//   part 3: C22 = alpha * U7 + beta * C22, U7 = ((P1 + P6) + P7) + P5
 template <int PART>
 __global__ void __launch_bounds__(128) quad_post_kernel(QuadPost q) {
     const long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -367,11 +371,13 @@ __global__ void __launch_bounds__(128) quad_post_kernel(QuadPost q) {
             put(q.c[0], add4(P(0), P(1)));
         } else {
             const float4 U2 = add4(P(0), P(5));
-            const float4 U3 = add4(U2, P(6));
-            const float4 U4 = add4(U2, P(4));
-            put(q.c[1], add4(U4, P(2)));   // U5 = U4 + P3
-            put(q.c[2], sub4(U3, P(3)));   // U6 = U3 - P4
-            put(q.c[3], add4(U3, P(4)));   // U7 = U3 + P5
+            if (PART == 1) {
+                put(q.c[1], add4(add4(U2, P(4)), P(2)));   // U5 = U4 + P3, U4 = U2 + P5
+            } else {
+                const float4 U3 = add4(U2, P(6));
+                if (PART == 2) put(q.c[2], sub4(U3, P(3)));   // U6 = U3 - P4
+                else put(q.c[3], add4(U3, P(4)));             // U7 = U3 + P5
+            }
         }
     }
 }
@@ -846,8 +852,13 @@ cudaError_t launch_quad_pre(const QuadPre& q, int side_b, cudaStream_t stream) {
 cudaError_t launch_quad_post(const QuadPost& q, int part, cudaStream_t stream) {
     if (q.h <= 0 || q.w <= 0) return cudaSuccess;
     dim3 grid((unsigned)((q.w + 511) / 512), gy(q.h));
-    if (part == 0) quad_post_kernel<0><<<grid, 128, 0, stream>>>(q);
-    else quad_post_kernel<1><<<grid, 128, 0, stream>>>(q);
+    switch (part) {
+        case 0: quad_post_kernel<0><<<grid, 128, 0, stream>>>(q); break;
+        case 1: quad_post_kernel<1><<<grid, 128, 0, stream>>>(q); break;
+        case 2: quad_post_kernel<2><<<grid, 128, 0, stream>>>(q); break;
+        case 3: quad_post_kernel<3><<<grid, 128, 0, stream>>>(q); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

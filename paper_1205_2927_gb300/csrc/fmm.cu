@@ -191,7 +191,7 @@ struct fmm_plan_s {
     char* child_ws = nullptr;
     size_t child_ws_bytes = 0;
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-    cudaEvent_t hev[6] = {};
+    cudaEvent_t hev[8] = {};
     // FP16x3: device operand scales {s_a, s_b} and reduction scratch, inside the status block
     float* fp16_scale() const { return reinterpret_cast<float*>(status + 16); }
     unsigned* fp16_scratch() const { return status + 24; }
@@ -1134,43 +1134,58 @@ fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B
         FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[4], 0));
         FMM_TRY(outC(0));
     } else {
-        // transfers in order of first use
+        // Transfers in order of first use, products in an order that lets each
+        // C quadrant leave as soon as its U-chain is complete:
+        //   P1, P2 -> C11;  T sums (all of B) -> P4;  S sums (A21 last) -> P6, P7
+        //   -> C21;  P5 -> C22;  P3 -> C12.
+        // Only the last quadrant's device-to-host copy is not hidden.
         FMM_TRY(inA(0)); FMM_TRY(inB(0));                        // A11, B11 -> P1
-        if (beta != 0.0f) for (int i = 0; i < 4; ++i) FMM_TRY(inC(i));
         FMM_CUDA(cudaEventRecord(ev[1], p->s_h2d));
         FMM_TRY(inA(1)); FMM_TRY(inB(2));                        // A12, B21 -> P2
         FMM_CUDA(cudaEventRecord(ev[2], p->s_h2d));
-        FMM_TRY(inA(2)); FMM_TRY(inA(3)); FMM_TRY(inB(1)); FMM_TRY(inB(3));
+        if (beta != 0.0f) FMM_TRY(inC(0));
+        FMM_CUDA(cudaEventRecord(ev[6], p->s_h2d));              // C11 (beta != 0)
+        FMM_TRY(inA(3)); FMM_TRY(inB(1)); FMM_TRY(inB(3));       // A22, B12, B22 -> T sums, P4
         FMM_CUDA(cudaEventRecord(ev[3], p->s_h2d));
+        FMM_TRY(inA(2));                                         // A21 -> S sums
+        FMM_CUDA(cudaEventRecord(ev[5], p->s_h2d));
+        if (beta != 0.0f) for (int i = 1; i < 4; ++i) FMM_TRY(inC(i));
+        FMM_CUDA(cudaEventRecord(ev[7], p->s_h2d));              // C12, C21, C22 (beta != 0)
         float* P[7];
         for (int i = 0; i < 7; ++i) P[i] = q[16 + i];
-        FMM_CUDA(cudaStreamWaitEvent(stream, ev[1], 0));
-        FMM_TRY(execute(c, 1.f, q[0], q[4], 0.f, P[0], stream));   // P1 = A11 B11
-        FMM_CUDA(cudaStreamWaitEvent(stream, ev[2], 0));
-        FMM_TRY(execute(c, 1.f, q[1], q[6], 0.f, P[1], stream));   // P2 = A12 B21
         QuadPost qp{};
         for (int i = 0; i < 7; ++i) qp.p[i] = P[i];
         for (int i = 0; i < 4; ++i) qp.c[i] = q[23 + i];
         qp.ld = hn; qp.h = hm; qp.w = hn; qp.alpha = alpha; qp.beta = beta;
-        FMM_CUDA(launch_quad_post(qp, 0, stream));                // C11 = alpha U1 + beta C11
-        FMM_CUDA(cudaEventRecord(ev[4], stream));
-        FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[4], 0));
-        FMM_TRY(outC(0));
-        FMM_CUDA(cudaStreamWaitEvent(stream, ev[3], 0));
+        // C quadrant i is formed on `stream`, then copied out on the d2h stream
+        auto post_out = [&](int i) -> fmm_status_t {
+            FMM_CUDA(launch_quad_post(qp, i, stream));
+            FMM_CUDA(cudaEventRecord(ev[4], stream));
+            FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[4], 0));
+            return outC(i);
+        };
         QuadPre pa{{q[0], q[1], q[2], q[3]}, {q[8], q[9], q[10], q[11]}, hk, hm, hk};
         QuadPre pb{{q[4], q[5], q[6], q[7]}, {q[12], q[13], q[14], q[15]}, hn, hk, hn};
-        FMM_CUDA(launch_quad_pre(pa, 0, stream));                 // S1..S4
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[1], 0));
+        FMM_TRY(execute(c, 1.f, q[0], q[4], 0.f, P[0], stream));   // P1 = A11 B11
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[2], 0));
+        FMM_TRY(execute(c, 1.f, q[1], q[6], 0.f, P[1], stream));   // P2 = A12 B21
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[6], 0));
+        FMM_TRY(post_out(0));                                      // C11 = alpha U1 + beta C11
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[3], 0));
         FMM_CUDA(launch_quad_pre(pb, 1, stream));                 // T1..T4
-        FMM_TRY(execute(c, 1.f, q[11], q[7], 0.f, P[2], stream));  // P3 = S4 B22
         FMM_TRY(execute(c, 1.f, q[3], q[15], 0.f, P[3], stream));  // P4 = A22 T4
-        FMM_TRY(execute(c, 1.f, q[8], q[12], 0.f, P[4], stream));  // P5 = S1 T1
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[5], 0));
+        FMM_CUDA(launch_quad_pre(pa, 0, stream));                 // S1..S4
         FMM_TRY(execute(c, 1.f, q[9], q[13], 0.f, P[5], stream));  // P6 = S2 T2
         FMM_TRY(execute(c, 1.f, q[10], q[14], 0.f, P[6], stream)); // P7 = S3 T3
-        FMM_CUDA(launch_quad_post(qp, 1, stream));                // C12, C21, C22
-        FMM_CUDA(cudaEventRecord(ev[5], stream));
-        FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[5], 0));
-        FMM_TRY(outC(1)); FMM_TRY(outC(2)); FMM_TRY(outC(3));
-        p->launches += 4;
+        FMM_CUDA(cudaStreamWaitEvent(stream, ev[7], 0));
+        FMM_TRY(post_out(2));                                      // C21 = alpha U6 + beta C21
+        FMM_TRY(execute(c, 1.f, q[8], q[12], 0.f, P[4], stream));  // P5 = S1 T1
+        FMM_TRY(post_out(3));                                      // C22 = alpha U7 + beta C22
+        FMM_TRY(execute(c, 1.f, q[11], q[7], 0.f, P[2], stream));  // P3 = S4 B22
+        FMM_TRY(post_out(1));                                      // C12 = alpha U5 + beta C12
+        p->launches += 6;
     }
 #undef FMM_TRY
     FMM_CUDA(cudaEventRecord(ev[0], p->s_d2h));
@@ -1557,7 +1572,7 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
         }
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
-        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming);
+        for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming);
         if (e != cudaSuccess) { fmm_free(p); return cuda_fail(e, "host-resident plan setup"); }
     }
     p->last_stream = (cudaStream_t)stream;

@@ -78,3 +78,23 @@ def test_host_resident_split_precision(F, prec):
     C = run_host(F, A, B, depth=2, precision=prec)
     ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
     assert np.array_equal(C, ref)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_host_resident_equals_device_resident(F, d):
+    # the streamed root forms each C quadrant with the same U-chain operations as
+    # the device-resident plan, and its child plan uses the same leaf tiles, so
+    # the two results agree bit for bit on float data (alpha, beta included)
+    import torch
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(2, 40 + d), "normal")
+    C0 = I.uniform((n, n), 41 + d)
+    host = run_host(F, A, B, C0, alpha=0.5, beta=-2.0, depth=d)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.from_numpy(C0).cuda()
+    p = F.Plan(n, n, n, depth=d)
+    p(dA, dB, dC, alpha=0.5, beta=-2.0)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    p.close()
+    assert np.array_equal(host, dC.cpu().numpy())
