@@ -1,0 +1,155 @@
+"""GPU parity at the benchmark's full sizes, in the launch configurations the
+bench times, on sampled outputs the oracle computes one row at a time.
+
+Each case checks (1) the error metric ||C - C64||_max / (||A||_max ||B||_max K)
+on sampled rows (always including the first and last row and rows on either
+side of the recursion's quadrant boundaries) against float64 rows of the
+definition c_ij = sum_k a_ik b_kj, and (2) a Freivalds residual over the whole
+product, r = C x - A (B x) for a +-1 probe x in float64, which bounds every
+row: |r|_inf <= N max|C - C64| <= N * bound * max|A| max|B| K.
+"""
+import numpy as np
+import pytest
+
+import oracle.fmm_oracle as O
+from paper_1205_2927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP32_BOUND = 2e-6
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1205_2927_gb300 import fmm
+    return fmm
+
+
+def sample_rows(m, depth, seed, extra=4):
+    """First/last rows, rows either side of every quadrant boundary of the
+    top recursion levels, and a few seeded random rows."""
+    rows = {0, m - 1}
+    for level in range(1, min(depth, 3) + 1):
+        parts = 1 << level
+        for p in range(1, parts):
+            b = (m * p) // parts
+            rows.update({b - 1, b})
+    rng = np.random.default_rng(seed)
+    rows.update(int(r) for r in rng.integers(0, m, extra))
+    return sorted(r for r in rows if 0 <= r < m)
+
+
+def check(A, B, C, rows, bound, x_seed):
+    k = A.shape[1]
+    den = float(np.abs(A).max()) * float(np.abs(B).max()) * k
+    ref = O.classical_rows(A, B, rows)
+    err = float(np.max(np.abs(C[rows].astype(np.float64) - ref))) / den
+    assert err <= bound, (err, bound)
+    x = I.rademacher(B.shape[1], x_seed)
+    r = O.freivalds(A, B, C, x)
+    assert float(np.max(np.abs(r))) <= B.shape[1] * bound * den, float(np.max(np.abs(r))) / den
+    return err
+
+
+def device_run(F, A, B, **kw):
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((m, n), device="cuda")
+    p = F.Plan(m, n, k, **kw)
+    p(dA, dB, dC)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    info = p.info
+    p.close()
+    C = dC.cpu().numpy()
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    return C, info
+
+
+def test_square_16384_bench_configuration(F):
+    # the bench's default launch: fixed planner, cut-off 4096 -> depth 2, CTA-pair leaves
+    n = 16384
+    A, B = I.operands(n, n, n, I.seed_for(2, 0))
+    C, info = device_run(F, A, B, precision="fp32", cutoff=4096)
+    assert (info["depth"], info["leaf_tile"]) == (2, 512)
+    check(A, B, C, sample_rows(n, 2, 1), FP32_BOUND, I.seed_for(2, 90))
+
+
+@pytest.mark.parametrize("odd", ["pad", "peel"])
+def test_odd_19000_depth_2(F, odd):
+    n = 19000
+    A, B = I.operands(n, n, n, I.seed_for(2, 19), "normal")
+    C, info = device_run(F, A, B, depth=2, odd=odd)
+    assert info["depth"] == 2
+    check(A, B, C, sample_rows(n, 2, 2), FP32_BOUND, I.seed_for(2, 91))
+
+
+@pytest.mark.parametrize("prec,dist,d,bound", [("fp32", "loguniform", 2, FP32_BOUND),
+                                               ("fp16x3", "normal", 2, FP32_BOUND),
+                                               ("bf16x3", "loguniform", 3, 5e-5),
+                                               ("tf32", "normal", 0, 5e-5)])
+def test_rectangular_19000x12000x15000_split_precision(F, prec, dist, d, bound):
+    m, k, n = 19000, 12000, 15000
+    A, B = I.operands(m, k, n, I.seed_for(3, m % 89), dist)
+    C, info = device_run(F, A, B, depth=d, precision=prec)
+    assert info["depth"] == d
+    assert np.all(np.isfinite(C[::97]))
+    check(A, B, C, sample_rows(m, d, 3), bound, I.seed_for(3, 92))
+
+
+def test_batched_512_uneven(F):
+    import torch
+    shapes = I.batched_shapes(512, I.seed_for(4, 0))
+    As = [I.uniform((m, k), I.seed_for(4, 1) + 3 * i) for i, (m, k, n) in enumerate(shapes)]
+    Bs = [I.uniform((k, n), I.seed_for(4, 2) + 3 * i) for i, (m, k, n) in enumerate(shapes)]
+    dA = [torch.from_numpy(a).cuda() for a in As]
+    dB = [torch.from_numpy(b).cuda() for b in Bs]
+    dC = [torch.empty((m, n), device="cuda") for m, k, n in shapes]
+    bp = F.BatchedPlan(dA, dB, dC, leaf_tile=256, cutoff=1024)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bp.run(s)   # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    for c in dC:
+        c.fill_(float("nan"))
+    with torch.cuda.graph(g):
+        bp.run(torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    depths = bp.info()["depths"]
+    assert any(d > 0 for d in depths) and any(d == 0 for d in depths)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for i, (m, k, n) in enumerate(shapes):
+        C = dC[i].cpu().numpy()
+        assert np.all(np.isfinite(C))
+        rows = sorted({0, m - 1, int(rng.integers(0, m))})
+        den = float(np.abs(As[i]).max()) * float(np.abs(Bs[i]).max()) * k
+        err = float(np.max(np.abs(C[rows].astype(np.float64) - O.classical_rows(As[i], Bs[i], rows)))) / den
+        worst = max(worst, err)
+    assert worst <= FP32_BOUND, worst
+    bp.close()
+
+
+def test_host_resident_16384_equals_device(F):
+    # the bench's end-to-end call (pinned host operands, transfers inside)
+    # against the device-resident plan of the same depth, bit for bit
+    import torch
+    n = 16384
+    A, B = I.operands(n, n, n, I.seed_for(2, 1))
+    dev, _ = device_run(F, A, B, depth=2)
+    hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    hC = torch.full((n, n), float("nan")).pin_memory()
+    p = F.Plan(n, n, n, depth=2, host_operands=1)
+    p(hA, hB, hC)
+    torch.cuda.current_stream().synchronize()
+    assert p.device_status() == 0
+    p.close()
+    assert np.array_equal(hC.numpy(), dev)
+    check(A, B, dev, sample_rows(n, 2, 4, extra=2), FP32_BOUND, I.seed_for(2, 93))
