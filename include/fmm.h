@@ -85,8 +85,8 @@ typedef struct {
     int depth;                 /* recursion levels; -1 = chosen by the planner */
     int cutoff;                /* planner: smallest leaf dimension worth a level (elements) */
     int leaf_tile;             /* leaf tile: 128 or 256 (128 x N tile on one SM), 512 (256 x 256
-                                  tile on a CTA pair; FP32, BF16X3, FP16X3 on device operands,
-                                  else 256); 0 = chosen with the depth */
+                                  tile on a pair of SMs; batched plans and a peeled border use
+                                  256 instead); 0 = chosen with the depth */
     fmm_precision_t precision;
     fmm_odd_t odd;
     fmm_planner_t planner;
@@ -203,8 +203,8 @@ fmm_status_t fmm_residual(int64_t M, int64_t N, int64_t K, const float* A, int64
 
 /* ---------------------------------------------------------------- planner
  * Candidate plans of a problem: depth 0..4 (a level only while every leaf
- * dimension stays >= 128) x leaf tile {128, 256, 512} (512 only for the
- * pre-split precisions and leaves of at least 256 x 256), restricted by
+ * dimension stays >= 128) x leaf tile {128, 256, 512} (512 only for leaves
+ * of at least 256 x 256), restricted by
  * opt->depth / opt->leaf_tile when those are set.  The paper's fixed
  * thresholds (Table 2, the recursion point of Sec. 3.1) never ask whether one
  * more split would pay on the machine at hand; these planners measure or

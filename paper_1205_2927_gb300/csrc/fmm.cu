@@ -381,12 +381,12 @@ int fixed_depth(long long M, long long N, long long K, int cutoff) {
     return d;
 }
 
-// Leaf tile when the caller leaves it open: the CTA-pair 256 x 256 tile for the
-// pre-split precisions once both output sides of every leaf reach 1024 (from
-// there on it is at least as fast as the single-CTA tile and halves the
-// per-SM operand traffic), the single-CTA 128 x 256 tile otherwise.
+// Leaf tile when the caller leaves it open: the CTA-pair 256 x 256 tile once
+// both output sides of every leaf reach 1024 (from there on it is at least as
+// fast as the single-CTA tile and cuts the per-SM operand traffic by a third),
+// the single-CTA 128 x 256 tile otherwise.
 int auto_tile(long long M, long long N, int depth, const fmm_options_t& o) {
-    if (o.precision == FMM_PREC_TF32) return 256;
+    (void)o;
     const long long mn = M < N ? M : N;
     return (mn >> depth) >= 1024 ? 512 : 256;
 }
@@ -483,7 +483,8 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
     memset(&args, 0, sizeof(args));
     fmm_status_t s;
     if ((s = encode_map(&args.maps[0], Aop, p->K, p->M, 1, lda, p->M * lda, kBM)) != FMM_OK) return s;
-    if ((s = encode_map(&args.maps[1], p->Bt, p->K, p->N, 1, p->ld_bt, p->N * p->ld_bt, p->bn)) != FMM_OK) return s;
+    if ((s = encode_map(&args.maps[1], p->Bt, p->K, p->N, 1, p->ld_bt, p->N * p->ld_bt, p->pair ? 128 : p->bn)) != FMM_OK)
+        return s;
     GemmGroup& G = args.groups[0];
     G.M = (int)p->M; G.N = (int)p->N; G.K = (int)p->K; G.batch = 1;
     G.C = C; G.ldc = p->ldc; G.c_batch_stride = 0;
@@ -657,7 +658,8 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
     if (Ll.full) {
         const long long batch = Lf.nodes;
         if ((s = encode_map(&maps[nm], Ll.achild, kk, mm, batch, kk, mm * kk, kBM)) != FMM_OK) return s;
-        if ((s = encode_map(&maps[nm + 1], Ll.bchild, kk, nn, batch, kk, nn * kk, p->bn)) != FMM_OK) return s;
+        if ((s = encode_map(&maps[nm + 1], Ll.bchild, kk, nn, batch, kk, nn * kk, p->pair ? 128 : p->bn)) != FMM_OK)
+            return s;
         GemmGroup& G = groups[ng++];
         memset(&G, 0, sizeof(G));
         G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)batch;
@@ -683,11 +685,12 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
         if ((s = encode_map(&maps[b0 + 3 + j], Ll.achild + j * mm * kk, kk, mm, nodes, kk, 4 * mm * kk, kBM)) != FMM_OK)
             return s;
     // B side (transposed): b0+7..9 views Y0, Y1, Y3; b0+10..13 sums T1..T4
-    if ((s = encode_map(&maps[b0 + 7], qb(0, 0), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
-    if ((s = encode_map(&maps[b0 + 8], qb(0, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
-    if ((s = encode_map(&maps[b0 + 9], qb(1, 1), kk, nn, nodes, ka, Ll.n * ka, p->bn)) != FMM_OK) return s;
+    const int bbox = p->pair ? 128 : p->bn;
+    if ((s = encode_map(&maps[b0 + 7], qb(0, 0), kk, nn, nodes, ka, Ll.n * ka, bbox)) != FMM_OK) return s;
+    if ((s = encode_map(&maps[b0 + 8], qb(0, 1), kk, nn, nodes, ka, Ll.n * ka, bbox)) != FMM_OK) return s;
+    if ((s = encode_map(&maps[b0 + 9], qb(1, 1), kk, nn, nodes, ka, Ll.n * ka, bbox)) != FMM_OK) return s;
     for (int j = 0; j < 4; ++j)
-        if ((s = encode_map(&maps[b0 + 10 + j], Ll.bchild + j * nn * kk, kk, nn, nodes, kk, 4 * nn * kk, p->bn)) !=
+        if ((s = encode_map(&maps[b0 + 10 + j], Ll.bchild + j * nn * kk, kk, nn, nodes, kk, 4 * nn * kk, bbox)) !=
             FMM_OK)
             return s;
     //                       P1  P2  P3  P4  P5  P6  P7
@@ -1010,8 +1013,8 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
     t.pre16 = 0;
     t.pair = 0;
     if (t.bn == 512) t.bn = 256;   // the pair tile is 256 wide: set below when the plan can use it
+    if (!t.host) t.pair = bn == 512 ? 1 : 0;
     if (!t.host && o.precision != FMM_PREC_TF32) {
-        t.pair = bn == 512 ? 1 : 0;
         t.pre16 = 1;
         t.split_kind = o.precision == FMM_PREC_BF16X3   ? kSplitBF16
                        : o.precision == FMM_PREC_FP16X3 ? kSplitFP16
@@ -1041,8 +1044,8 @@ int candidates(long long M, long long N, long long K, const fmm_options_t& o, Ca
         if (o.depth >= 0 && d != o.depth) continue;
         for (int bn : {128, 256, 512}) {
             if (o.leaf_tile && bn != o.leaf_tile) continue;
-            // CTA-pair tiles: pre-split precisions, leaves of at least one pair tile
-            if (bn == 512 && (o.precision == FMM_PREC_TF32 || (std::min(M, N) >> d) < 256)) continue;
+            // CTA-pair tiles: leaves of at least one pair tile
+            if (bn == 512 && (std::min(M, N) >> d) < 256) continue;
             out[n++] = Cand{d, bn};
         }
     }
@@ -1686,7 +1689,7 @@ fmm_status_t fmm_get_device_status(fmm_plan_t p) {
 fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precision, int* odd, int* algo) {
     if (!p) return FMM_ERR_INVALID_ARG;
     if (depth) *depth = p->depth;
-    if (leaf_tile) *leaf_tile = (p->pair || (p->host && p->tile_req == 512 && p->opt.precision != FMM_PREC_TF32)) ? 512 : p->bn;
+    if (leaf_tile) *leaf_tile = (p->pair || (p->host && p->tile_req == 512)) ? 512 : p->bn;
     if (precision) *precision = (int)p->opt.precision;
     if (odd) *odd = (int)p->opt.odd;
     if (algo) *algo = (int)p->opt.algo;

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pair-of-SMs variant (cta_group::2) for the pre-split modes.  A cluster of two
+// Pair-of-SMs variant (cta_group::2) for the pre-split modes and TF32.  A cluster of two
 // CTAs computes one 256 x 256 output tile: CTA r (cluster rank) loads rows
 // [128 r, 128 r + 128) of the A tile and of the B^T tile into its own shared
 // memory; CTA 0 issues M = 256 tcgen05.mma instructions that read both CTAs'
@@ -417,10 +417,12 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
 //              CTA's producer waits on its own empty barrier
 template <int MODE>
 struct PairCfg {
+    static constexpr bool kPlain = MODE == kLeafTF32;          // fp32 A | B tiles, 128-byte rows, one product
     static constexpr int kRows = 128;                          // rows per CTA of A and of B^T
-    static constexpr int kStageBytes = 4 * kRows * 64;         // A hi | B hi | A lo | B lo, 64-byte rows
+    // split planes: A hi | B hi | A lo | B lo with 64-byte rows; TF32: A | B with 128-byte rows
+    static constexpr int kStageBytes = 4 * kRows * 64;
     static constexpr int kStages = 6;
-    static constexpr int kKB = MODE == kLeaf3xTF32P ? 16 : 32; // K elements per 64-byte row
+    static constexpr int kKB = MODE == kLeaf3xTF32P ? 16 : 32;   // K elements per stage (one row)
     static constexpr int kTmemCols = 512;                      // 2 x 256-column accumulators
     static constexpr int kBarBytes = 256;
     static constexpr int kThreads = 256;
@@ -502,12 +504,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                     // zero, which the arming arrival brings back
                     if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * Cfg::kStageBytes);
                     const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
-                    const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
                     const int x = kb * Cfg::kKB;
-                    tma_load_3d_pair(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
-                    tma_load_3d_pair(bh, maps + G.map_b, full_bar(stage), x, b0, bb);
-                    tma_load_3d_pair(al, maps + G.map_a_lo, full_bar(stage), x, a0, ab);
-                    tma_load_3d_pair(bl, maps + G.map_b_lo, full_bar(stage), x, b0, bb);
+                    if constexpr (Cfg::kPlain) {
+                        tma_load_3d_pair(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
+                        tma_load_3d_pair(ah + Cfg::kRows * 128, maps + G.map_b, full_bar(stage), x, b0, bb);
+                    } else {
+                        const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+                        tma_load_3d_pair(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
+                        tma_load_3d_pair(bh, maps + G.map_b, full_bar(stage), x, b0, bb);
+                        tma_load_3d_pair(al, maps + G.map_a_lo, full_bar(stage), x, a0, ab);
+                        tma_load_3d_pair(bl, maps + G.map_b_lo, full_bar(stage), x, b0, bb);
+                    }
                     ++issued;
                     if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
                 }
@@ -519,7 +526,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (CTA 0)
         if (lane == 0 && rank == 0) {
-            constexpr uint32_t fmt = MODE == kLeaf3xTF32P ? 2u : (MODE == kLeafBF16x3P ? 1u : 0u);
+            constexpr uint32_t fmt = (MODE == kLeaf3xTF32P || MODE == kLeafTF32) ? 2u : (MODE == kLeafBF16x3P ? 1u : 0u);
             constexpr uint32_t idesc = make_idesc(fmt, 256, 256);
             int stage = 0;
             uint32_t phase = 0;
@@ -540,22 +547,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                     if (!mbar_wait(full_bar(stage), phase, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t ah = stage0 + stage * Cfg::kStageBytes;
-                    const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+                    if constexpr (Cfg::kPlain) {
+                        // fp32 tiles with 128-byte rows (32 elements of K): 4 MMAs of K = 8
+                        const uint32_t bh = ah + Cfg::kRows * 128;
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-                        const uint64_t ahd = sdesc_kmajor_sw64(ah + kk * 32);
-                        const uint64_t bhd = sdesc_kmajor_sw64(bh + kk * 32);
-                        const uint64_t ald = sdesc_kmajor_sw64(al + kk * 32);
-                        const uint64_t bld = sdesc_kmajor_sw64(bl + kk * 32);
-                        if constexpr (MODE == kLeaf3xTF32P) {
-                            mma_tf32_pair(d, ald, bhd, idesc, first);  // lo_a * hi_b
-                            mma_tf32_pair(d, ahd, bld, idesc, 1u);     // hi_a * lo_b
-                            mma_tf32_pair(d, ahd, bhd, idesc, 1u);     // hi_a * hi_b
-                        } else {
-                            mma_f16_pair(d, ald, bhd, idesc, first);
-                            mma_f16_pair(d, ahd, bld, idesc, 1u);
-                            mma_f16_pair(d, ahd, bhd, idesc, 1u);
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_tf32_pair(d, sdesc_kmajor_sw128(ah + kk * 32), sdesc_kmajor_sw128(bh + kk * 32), idesc,
+                                          (kb == 0 && kk == 0) ? 0u : 1u);
+                    } else {
+                        const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+                            const uint64_t ahd = sdesc_kmajor_sw64(ah + kk * 32);
+                            const uint64_t bhd = sdesc_kmajor_sw64(bh + kk * 32);
+                            const uint64_t ald = sdesc_kmajor_sw64(al + kk * 32);
+                            const uint64_t bld = sdesc_kmajor_sw64(bl + kk * 32);
+                            if constexpr (MODE == kLeaf3xTF32P) {
+                                mma_tf32_pair(d, ald, bhd, idesc, first);  // lo_a * hi_b
+                                mma_tf32_pair(d, ahd, bld, idesc, 1u);     // hi_a * lo_b
+                                mma_tf32_pair(d, ahd, bhd, idesc, 1u);     // hi_a * hi_b
+                            } else {
+                                mma_f16_pair(d, ald, bhd, idesc, first);
+                                mma_f16_pair(d, ahd, bld, idesc, 1u);
+                                mma_f16_pair(d, ahd, bhd, idesc, 1u);
+                            }
                         }
                     }
                     mma_commit_pair(empty_bar(stage), (uint16_t)0x3);
@@ -686,6 +702,7 @@ static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStrea
 
 cudaError_t launch_leaf_gemm_pair(const GemmArgs& args, int mode, int num_sms, cudaStream_t stream) {
     switch (mode) {
+        case kLeafTF32: return launch_pair_impl<kLeafTF32>(args, num_sms, stream);
         case kLeaf3xTF32P: return launch_pair_impl<kLeaf3xTF32P>(args, num_sms, stream);
         case kLeafBF16x3P: return launch_pair_impl<kLeafBF16x3P>(args, num_sms, stream);
         case kLeafFP16x3P: return launch_pair_impl<kLeafFP16x3P>(args, num_sms, stream);

@@ -302,9 +302,9 @@ def test_deep_recursion_bit_exact(fmm, prec, m, k, n, d):
 
 # --- leaves on CTA pairs (cta_group::2, 256 x 256 tiles) ----------------------
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3", "tf32"])
 @pytest.mark.parametrize("m,k,n,d", [(256, 64, 256, 0), (300, 200, 260, 0), (777, 333, 515, 0), (1100, 900, 1300, 2),
-                                     (512, 512, 512, 3), (1, 1, 1, 0)])
+                                     (512, 512, 512, 3), (1, 1, 1, 0), (640, 480, 704, 1)])
 def test_pair_leaves_bit_exact(fmm, prec, m, k, n, d):
     A = I.small_int((m, k), 16000 + m + d, r=2)
     B = I.small_int((k, n), 16100 + n + d, r=2)
