@@ -184,6 +184,15 @@ fmm_status_t fmm_get_device_status(fmm_plan_t plan);
  * Either pointer may be NULL. */
 fmm_status_t fmm_plan_phase_bytes(fmm_plan_t plan, double* pre_bytes, double* post_bytes);
 
+/* Failure-path self-test of the device waits.  Launches one block on `stream`
+ * whose thread waits, with the bounded wait every kernel pipeline of the
+ * library uses but a limit of limit_ns (1e6 .. 1e10 ns), on a barrier that
+ * nothing signals.  The wait runs out, sets the timeout bit of the plan's
+ * device status word and the kernel returns, so the context stays usable:
+ * fmm_get_device_status then reports FMM_ERR_TIMEOUT (and clears the word).
+ * FMM_ERR_INVALID_ARG for a NULL plan or a limit out of range.  Asynchronous. */
+fmm_status_t fmm_wait_selftest(fmm_plan_t plan, int64_t limit_ns, fmm_stream_t stream);
+
 /* Plan inspection: depth, leaf tile width, precision and odd mode the plan
  * uses (after the planner ran); any pointer may be NULL. */
 fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* precision,

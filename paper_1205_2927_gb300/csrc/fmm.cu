@@ -1686,6 +1686,14 @@ fmm_status_t fmm_get_device_status(fmm_plan_t p) {
     return w ? FMM_ERR_CUDA : FMM_OK;
 }
 
+fmm_status_t fmm_wait_selftest(fmm_plan_t p, int64_t limit_ns, fmm_stream_t stream_) {
+    if (!p || limit_ns < 1000000 || limit_ns > 10000000000LL) return FMM_ERR_INVALID_ARG;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    p->last_stream = stream;
+    FMM_CUDA(launch_wait_selftest(p->status, (unsigned long long)limit_ns, stream));
+    return FMM_OK;
+}
+
 fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precision, int* odd, int* algo) {
     if (!p) return FMM_ERR_INVALID_ARG;
     if (depth) *depth = p->depth;

@@ -58,6 +58,9 @@ size_t leaf_smem_bytes(int mode, int bn);
 // tiles_n must be counted in 256-row / 256-column units, B maps with 128-row
 // boxes).
 cudaError_t launch_leaf_gemm_pair(const GemmArgs& args, int mode, int num_sms, cudaStream_t stream);
+// One bounded wait on a barrier nothing signals: sets the timeout bit of *status
+// after limit_ns and returns (the failure path of every pipeline wait).
+cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit_ns, cudaStream_t stream);
 
 // ------------------------------------------------------------ additions
 // A matrix operand view: `nodes` matrices of rows x cols, node i at

@@ -55,14 +55,14 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity)
 // the block is aborting or the time limit ran out (then the status word and the
 // block's abort flag are set).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          unsigned* status) {
+                                          unsigned* status, unsigned long long limit_ns = FMM_WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > FMM_WAIT_LIMIT_NS) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicOr(status, FMM_DEV_TIMEOUT_BIT);
                 *abort_flag = 1;
                 return false;

@@ -14,6 +14,8 @@ import os
 from . import build as _build
 
 FMM_OK = 0
+FMM_ERR_INVALID_ARG = 1
+FMM_ERR_TIMEOUT = 7
 STATUS_NAMES = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_ALIGNMENT", 3: "FMM_ERR_SHAPE_MISMATCH",
                 4: "FMM_ERR_OOM", 5: "FMM_ERR_CUDA", 6: "FMM_ERR_UNSUPPORTED", 7: "FMM_ERR_TIMEOUT",
                 8: "FMM_ERR_NO_DEVICE", 9: "FMM_ERR_WORKSPACE"}
@@ -78,6 +80,8 @@ def _load():
     lib.fmm_plan_profile_read.restype = C.c_int
     lib.fmm_plan_phase_bytes.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.fmm_plan_phase_bytes.restype = C.c_int
+    lib.fmm_wait_selftest.argtypes = [vp, i64, vp]
+    lib.fmm_wait_selftest.restype = C.c_int
     return lib
 
 
@@ -204,6 +208,10 @@ class Plan:
 
     def profile_read(self):
         return fmm_plan_profile_read(self.handle)
+
+    def wait_selftest(self, limit_ns=20_000_000, stream=None):
+        """Run the device-wait failure path once (see fmm_wait_selftest)."""
+        _check(_lib.fmm_wait_selftest(self.handle, int(limit_ns), _stream_ptr(stream)), "fmm_wait_selftest")
 
     def phase_bytes(self):
         """Algorithmic bytes of the last call's addition phases (pre_bytes, post_bytes)."""

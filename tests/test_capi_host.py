@@ -91,6 +91,7 @@ def test_gemm_rejects_null_plan(F):
     assert F.library().fmm_gemm(None, C.c_float(1), None, None, C.c_float(0), None, None) == 1
     F.library().fmm_free(None)  # NULL-safe
     assert F.library().fmm_plan_phase_bytes(None, None, None) == 1
+    assert F.library().fmm_wait_selftest(None, 20_000_000, None) == 1
 
 
 def test_no_cpu_fallback_without_gpu(F):

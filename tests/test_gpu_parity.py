@@ -356,3 +356,27 @@ def test_phase_bytes_closed_forms(fmm):
     torch.cuda.synchronize()
     assert p.phase_bytes()["pre_bytes"] == 2 * n * n * 4 + 2 * 49 * h * h * 4
     p.close()
+
+
+# --- failure path of the bounded device waits -----------------------------------
+
+def test_wait_timeout_is_reported_and_context_stays_usable(fmm):
+    import time
+    import torch
+    n = 256
+    A = I.small_int((n, n), 71, r=2)
+    B = I.small_int((n, n), 72, r=2)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.empty((n, n), device="cuda")
+    p = fmm.Plan(n, n, n, depth=1)
+    t0 = time.perf_counter()
+    p.wait_selftest(limit_ns=20_000_000)   # a barrier nothing signals, 20 ms limit
+    assert p.device_status() == fmm.FMM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert p.device_status() == fmm.FMM_OK   # the read cleared the word
+    p(dA, dB, dC)
+    torch.cuda.synchronize()
+    assert p.device_status() == fmm.FMM_OK
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(dC.cpu().numpy(), ref)
+    p.close()
