@@ -386,6 +386,9 @@ __global__ void __launch_bounds__(128) quad_post_kernel(QuadPost q) {
 // Split four consecutive values into the planes at element offset o.
 //   bf16 / fp16: x * s = hi + lo (+ residual), hi = rn16(x s), lo = rn16(x s - hi)
 //   tf32:        hi = x (the tensor core reads trunc_tf32(x)), lo = rn_tf32(x - trunc_tf32(x))
+// The planes are written with evict-first (streaming) stores: they are read by
+// the leaf launch only after far more data than L2 holds has passed, and they
+// must not push out the operand lines a fused pass reads again.
 template <int KIND>
 __device__ __forceinline__ void split_store(void* hi_plane, void* lo_plane, long long o, float4 v, float sc) {
     if constexpr (KIND == kSplitTF32) {
@@ -394,8 +397,8 @@ __device__ __forceinline__ void split_store(void* hi_plane, void* lo_plane, long
         l.y = tf32_round_rne(v.y - tf32_trunc(v.y));
         l.z = tf32_round_rne(v.z - tf32_trunc(v.z));
         l.w = tf32_round_rne(v.w - tf32_trunc(v.w));
-        *reinterpret_cast<float4*>(static_cast<float*>(hi_plane) + o) = v;
-        *reinterpret_cast<float4*>(static_cast<float*>(lo_plane) + o) = l;
+        __stcs(reinterpret_cast<float4*>(static_cast<float*>(hi_plane) + o), v);
+        __stcs(reinterpret_cast<float4*>(static_cast<float*>(lo_plane) + o), l);
         return;
     }
     uint16_t* hi = static_cast<uint16_t*>(hi_plane) + o;
@@ -415,8 +418,8 @@ __device__ __forceinline__ void split_store(void* hi_plane, void* lo_plane, long
         h01 = *reinterpret_cast<const uint32_t*>(&a); h23 = *reinterpret_cast<const uint32_t*>(&b);
         l01 = *reinterpret_cast<const uint32_t*>(&c); l23 = *reinterpret_cast<const uint32_t*>(&d);
     }
-    *reinterpret_cast<uint2*>(hi) = make_uint2(h01, h23);
-    *reinterpret_cast<uint2*>(lo) = make_uint2(l01, l23);
+    __stcs(reinterpret_cast<uint2*>(hi), make_uint2(h01, h23));
+    __stcs(reinterpret_cast<uint2*>(lo), make_uint2(l01, l23));
 }
 
 // Same arithmetic as pre_add_kernel (all 7 children), output split into planes.
@@ -597,6 +600,107 @@ __global__ void __launch_bounds__(128) pre_add2_kernel(View P, long long h, long
     }
 }
 
+// Child i (product order) of an operand from its four quadrants, one element at
+// a time: the same fp32 operations as children7 computing only that child.
+template <int SIDE_B>
+__device__ __forceinline__ float child_of1(int i, float Q0, float Q1, float Q2, float Q3) {
+    if (!SIDE_B) {
+        switch (i) {
+            case 0: return Q0;
+            case 1: return Q1;
+            case 2: return Q1 - ((Q2 + Q3) - Q0);   // S4 = Q1 - S2
+            case 3: return Q3;
+            case 4: return Q2 + Q3;                 // S1
+            case 5: return (Q2 + Q3) - Q0;          // S2 = S1 - Q0
+            default: return Q0 - Q2;                // S3
+        }
+    }
+    switch (i) {
+        case 0: return Q0;
+        case 1: return Q1;
+        case 2: return Q3;
+        case 3: return (Q3 - (Q2 - Q0)) - Q1;       // T4 = T2 - Q1, T2 = Q3 - T1
+        case 4: return Q2 - Q0;                     // T1
+        case 5: return Q3 - (Q2 - Q0);              // T2
+        default: return Q3 - Q2;                    // T3
+    }
+}
+
+// One value into the planes at element offset o (evict-first stores).
+template <int KIND>
+__device__ __forceinline__ void split_store1(void* hi_plane, void* lo_plane, long long o, float v, float sc) {
+    if constexpr (KIND == kSplitTF32) {
+        __stcs(static_cast<float*>(hi_plane) + o, v);
+        __stcs(static_cast<float*>(lo_plane) + o, tf32_round_rne(v - tf32_trunc(v)));
+        return;
+    }
+    const float x = v * sc;
+    unsigned short h, l;
+    if constexpr (KIND == kSplitBF16) {
+        const __nv_bfloat16 a = __float2bfloat16_rn(x);
+        const __nv_bfloat16 b = __float2bfloat16_rn(x - __bfloat162float(a));
+        h = __bfloat16_as_ushort(a);
+        l = __bfloat16_as_ushort(b);
+    } else {
+        const __half a = __float2half_rn(x);
+        const __half b = __float2half_rn(x - __half2float(a));
+        h = __half_as_ushort(a);
+        l = __half_as_ushort(b);
+    }
+    __stcs(static_cast<unsigned short*>(hi_plane) + o, h);
+    __stcs(static_cast<unsigned short*>(lo_plane) + o, l);
+}
+
+// Pre-additions of three consecutive levels in one pass (the whole recursion
+// of a depth-3 plan): each node operand (8h x 8w, read through its view with
+// zero outside the valid window) -> its 343 great-grandchildren (h x w), split
+// planes at stack index node * 343 + (i * 7 + j) * 7 + l.  One element per
+// thread: the node's 64 sub-block values are loaded once, level-1 child i's
+// 4 x 4 sub-block values are formed from them, then level-2 child j's
+// quadrants, then its 7 children; the fp32 operations are those of three
+// pre_add passes.
+template <int SIDE_B, int KIND>
+__global__ void __launch_bounds__(256, 2) pre_add3_kernel(View P, long long h, long long w, Stack16 out,
+                                                       const float* __restrict__ scale) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= w) return;
+    const float sc = scale ? scale[SIDE_B] : 1.0f;
+    const long long node = blockIdx.z;
+    const float* base = P.ptr + node * P.node_stride;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        const long long o0 = (node * 343) * out.child_stride + r * out.ld + c;
+        float X[8][8];   // sub-block (a, b) of the node
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const long long row = a * h + r, col = b * w + c;
+                X[a][b] = (row < P.valid_rows && col < P.valid_cols) ? __ldg(base + row * P.ld + col) : 0.0f;
+            }
+#pragma unroll 1
+        for (int i = 0; i < 7; ++i) {
+            float Y[4][4];   // level-1 child i, sub-block (a, b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    Y[a][b] = child_of1<SIDE_B>(i, X[a][b], X[a][4 + b], X[4 + a][b], X[4 + a][4 + b]);
+#pragma unroll 1
+            for (int j = 0; j < 7; ++j) {
+                float Cj[4];   // level-2 child (i, j), quadrant t
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    Cj[t] = child_of1<SIDE_B>(j, Y[(t >> 1)][(t & 1)], Y[(t >> 1)][2 + (t & 1)],
+                                              Y[2 + (t >> 1)][(t & 1)], Y[2 + (t >> 1)][2 + (t & 1)]);
+#pragma unroll
+                for (int l = 0; l < 7; ++l)
+                    split_store1<KIND>(out.hi, out.lo, o0 + (i * 49 + j * 7 + l) * out.child_stride,
+                                       child_of1<SIDE_B>(l, Cj[0], Cj[1], Cj[2], Cj[3]), sc);
+            }
+        }
+    }
+}
+
 // Root B side of a depth-2 plan in one pass, straight from the caller's
 // row-major B (valid K x N, zero outside) into the 49 leaf operands of B^T,
 // split into planes.  Leaf position (n, k) of B^T sub-block (a, b) is
@@ -708,6 +812,63 @@ __global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict_
                 const long long rr = (long long)((q >> 1) * 2 + (t >> 1)) * h + r;
                 const long long cc = (long long)((q & 1) * 2 + (t & 1)) * w + c;
                 const float v = uchain_quadrant(q, Ct[0], Ct[1], Ct[2], Ct[3], Ct[4], Ct[5], Ct[6]);
+                if (!ROOT) {
+                    o[rr * ld_out + cc] = v;
+                } else if (rr < valid_rows && cc < valid_cols) {
+                    float* dst = o + rr * ld_out + cc;
+                    *dst = (beta != 0.0f) ? alpha * v + beta * *dst : alpha * v;
+                }
+            }
+        }
+    }
+}
+
+// Post-additions of three consecutive levels in one pass (the whole recursion
+// of a depth-3 plan, ROOT) or of a node's bottom three levels: for each node,
+// its 343 great-grandchild products P[node * 343 + (i * 7 + j) * 7 + l] (h x w,
+// row stride ld_in) -> the node output (8h x 8w).  One element per thread,
+// every product loaded once.  Level-2 outputs (the U-chain over l), then each
+// level-1 child's 16 values (the U-chain over j), then the node's 64 values
+// (the U-chain over i): the fp32 operations of three post_add passes.
+template <bool ROOT>
+__global__ void __launch_bounds__(128, 2) post_add3_kernel(const float* __restrict__ P, long long ld_in, long long cs,
+                                                        long long h, long long w, float* out, long long ld_out,
+                                                        long long out_ns, long long valid_rows, long long valid_cols,
+                                                        float alpha, float beta) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= w) return;
+    const long long node = blockIdx.z;
+    const float* base = P + node * 343 * cs;
+    float* o = out + node * out_ns;
+    for (long long r = blockIdx.y; r < h; r += gridDim.y) {
+        const float* pr = base + r * ld_in + c;
+        float o1[7][16];   // level-1 child i at (quadrant q1, sub-quadrant q2): [q1 * 4 + q2]
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            float o2[7][4];   // level-2 child (i, j), quadrant q2
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                float p[7];
+#pragma unroll
+                for (int l = 0; l < 7; ++l) p[l] = __ldg(pr + ((i * 7 + j) * 7 + l) * cs);
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2) o2[j][q2] = uchain_quadrant(q2, p[0], p[1], p[2], p[3], p[4], p[5], p[6]);
+            }
+#pragma unroll
+            for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2)
+                    o1[i][q1 * 4 + q2] = uchain_quadrant(q1, o2[0][q2], o2[1][q2], o2[2][q2], o2[3][q2], o2[4][q2],
+                                                         o2[5][q2], o2[6][q2]);
+        }
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {            // (q1, q2)
+            const int q1 = s >> 2, q2 = s & 3;
+#pragma unroll
+            for (int q0 = 0; q0 < 4; ++q0) {
+                const long long rr = (long long)(4 * (q0 >> 1) + 2 * (q1 >> 1) + (q2 >> 1)) * h + r;
+                const long long cc = (long long)(4 * (q0 & 1) + 2 * (q1 & 1) + (q2 & 1)) * w + c;
+                const float v = uchain_quadrant(q0, o1[0][s], o1[1][s], o1[2][s], o1[3][s], o1[4][s], o1[5][s], o1[6][s]);
                 if (!ROOT) {
                     o[rr * ld_out + cc] = v;
                 } else if (rr < valid_rows && cc < valid_cols) {
@@ -949,6 +1110,39 @@ cudaError_t launch_pre_add2_b_root(const float* B, long long ldb, long long K, l
         case kSplitFP16: pre_add2_b_root_kernel<kSplitFP16><<<grid, block, 0, stream>>>(B, ldb, K, N, h, w, out, scale); break;
         default: pre_add2_b_root_kernel<kSplitTF32><<<grid, block, 0, stream>>>(B, ldb, K, N, h, w, out, scale); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add3(const View& node, long long nodes, const Stack16& out, int side_b, int kind,
+                            const float* scale, cudaStream_t stream) {
+    const long long h = node.rows / 8, w = node.cols / 8;
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((w + 255) / 256), gy(h), (unsigned)nodes);
+#define FMM_PRE3(S, K) pre_add3_kernel<S, K><<<grid, 256, 0, stream>>>(node, h, w, out, scale)
+#define FMM_PRE3K(S)                                        \
+    switch (kind) {                                          \
+        case kSplitBF16: FMM_PRE3(S, kSplitBF16); break;    \
+        case kSplitFP16: FMM_PRE3(S, kSplitFP16); break;    \
+        default: FMM_PRE3(S, kSplitTF32); break;            \
+    }
+    if (side_b) { FMM_PRE3K(1) } else { FMM_PRE3K(0) }
+#undef FMM_PRE3K
+#undef FMM_PRE3
+    return cudaGetLastError();
+}
+
+cudaError_t launch_post_add3(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
+                             long long w, float* out, long long ld_out, long long out_node_stride,
+                             long long valid_rows, long long valid_cols, float alpha, float beta,
+                             cudaStream_t stream) {
+    if (h <= 0 || w <= 0 || nodes <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((w + 127) / 128), gy(h), (unsigned)nodes);
+    if (valid_rows >= 0)
+        post_add3_kernel<true><<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride,
+                                                         valid_rows, valid_cols, alpha, beta);
+    else
+        post_add3_kernel<false><<<grid, 128, 0, stream>>>(P, ld_in, child_stride, h, w, out, ld_out, out_node_stride,
+                                                          -1, -1, 1.f, 0.f);
     return cudaGetLastError();
 }
 

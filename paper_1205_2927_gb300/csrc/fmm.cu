@@ -172,16 +172,20 @@ struct fmm_plan_s {
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
     size_t es16() const { return split_kind == kSplitTF32 ? 4 : 2; }
-    // depth >= 3: the last two levels of pre-additions (split-plane plans) and of
+    // depth >= 4: the last two levels of pre-additions (split-plane plans) and of
     // post-additions run as one pass each; the middle level is never stored
-    bool fuse_pre() const { return pre16 && depth >= 3; }
-    bool fuse_post() const { return depth >= 3; }
+    bool fuse_pre() const { return pre16 && depth >= 4; }
+    bool fuse_post() const { return depth >= 4; }
     // depth 2: both levels at once from / into the caller's matrices
     bool fuse_root_pre() const { return pre16 && depth == 2; }
     bool fuse_root_post() const { return depth == 2; }
+    // depth 3: all three levels at once from / into the caller's matrices
+    bool fuse_root_pre3() const { return pre16 && depth == 3; }
+    bool fuse_root_post3() const { return depth == 3; }
     // algorithmic bytes (reads + writes the passes need) of the last call's
     // addition phases: [0] before the leaf launch, [1] after it
     double acct[2] = {0.0, 0.0};
+    float* bt_root = nullptr;   // depth-3 split-plane plans: B^T zero-padded to N0 x K0
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -303,6 +307,10 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             const long long per = L.full ? 7 : 4;
             if (p->fuse_pre() && l == d - 2) continue;   // written by neither pass: fused away
             if (p->fuse_root_pre() && l == 0) continue;   // fused away (both sides read the caller's operands)
+            if (p->fuse_root_pre3() && l < d - 1) {   // fused away; B^T of the root instead
+                if (l == 0) p->bt_root = cv.take<float>((size_t)(p->N0 * p->K0));
+                continue;
+            }
             if (p->pre16 && l == d - 1) {   // the leaves' operands, as split planes
                 p->ld16 = rup(C.k, 128 / (long long)p->es16());   // 128-byte row pitch
                 for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
@@ -316,6 +324,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
         for (int l = 1; l < d; ++l) {
             if ((p->fuse_post() || p->fuse_root_post()) && l == d - 1) continue;   // fused away
+            if (p->fuse_root_post3()) continue;
             Level& L = p->lv[l];
             L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
         }
@@ -559,6 +568,22 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
     const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
     const double pl = 2.0 * (double)p->es16();   // bytes per element of a hi + lo plane pair
     const double root_in = 4.0 * (double)(p->Mw * p->Kw + p->Kw * p->Nw);
+    if (p->fuse_root_pre3()) {
+        // all three levels at once: root -> the 343 leaf operands of each side
+        const Level& Lf = lv[3];
+        View va{A, p->lda, 0, p->M0, p->K0, p->Mw, p->Kw};
+        Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 343};
+        Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 343};
+        FMM_CUDA(launch_pre_add3(va, 1, sa, 0, kind, scale, stream));
+        // B: one zero-padded transposed copy, then the same pass on B^T
+        FMM_CUDA(launch_transpose(B, p->ldb, p->Kw, p->Nw, p->bt_root, p->K0, stream, p->N0, p->K0));
+        View vb{p->bt_root, p->K0, 0, p->N0, p->K0, p->N0, p->K0};
+        FMM_CUDA(launch_pre_add3(vb, 1, sb, 1, kind, scale, stream));
+        p->launches += 3;
+        p->acct[0] += root_in + 4.0 * (double)(p->Kw * p->Nw + p->N0 * p->K0) +
+                      343.0 * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
+        return FMM_OK;
+    }
     if (p->fuse_root_pre()) {
         // both levels at once: root -> the 49 leaf operands; the B side reads the
         // caller's row-major B and writes the K-major (transposed) leaf planes
@@ -713,6 +738,15 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
     Level* lv = p->lv;
     int top = d - 1;
     const double root_out = 4.0 * (double)(p->Mw * p->Nw) * (beta != 0.0f ? 2.0 : 1.0);
+    if (p->fuse_root_post3()) {
+        // all three levels at once: leaf products -> the caller's C
+        const Level& Lf = lv[3];
+        FMM_CUDA(launch_post_add3(p->P, Lf.n, Lf.m * Lf.n, 1, Lf.m, Lf.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
+                                  stream));
+        p->launches += 1;
+        p->acct[1] += 343.0 * 4.0 * (double)(Lf.m * Lf.n) + root_out;
+        return FMM_OK;
+    }
     if (p->fuse_root_post()) {
         // both levels at once: leaf products -> the caller's C (alpha, beta, valid window)
         const Level& Lf = lv[2];

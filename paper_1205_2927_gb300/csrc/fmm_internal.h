@@ -196,6 +196,15 @@ cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& ou
 // into the 49 leaf operands of B^T (h = N0 / 4 rows, w = K0 / 4 columns each).
 cudaError_t launch_pre_add2_b_root(const float* B, long long ldb, long long K, long long N, long long h, long long w,
                                    const Stack16& out, int kind, const float* scale, cudaStream_t stream);
+// Three levels at once (a depth-3 plan's whole recursion): node operands
+// (8h x 8w) -> 343 split leaf operands each; and 343 products per node -> the
+// node output (alpha / beta and the valid window at the root, valid_rows >= 0).
+cudaError_t launch_pre_add3(const View& node, long long nodes, const Stack16& out, int side_b, int kind,
+                            const float* scale, cudaStream_t stream);
+cudaError_t launch_post_add3(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
+                             long long w, float* out, long long ld_out, long long out_node_stride,
+                             long long valid_rows, long long valid_cols, float alpha, float beta,
+                             cudaStream_t stream);
 cudaError_t launch_post_add2(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,
                              long long w, float* out, long long ld_out, long long out_node_stride,
                              long long valid_rows, long long valid_cols, float alpha, float beta,

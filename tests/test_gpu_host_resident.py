@@ -80,7 +80,7 @@ def test_host_resident_split_precision(F, prec):
     assert np.array_equal(C, ref)
 
 
-@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
 def test_host_resident_equals_device_resident(F, d):
     # the streamed root forms each C quadrant with the same U-chain operations as
     # the device-resident plan, and its child plan uses the same leaf tiles, so
