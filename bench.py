@@ -504,7 +504,7 @@ def main():
     dB = torch.from_numpy(B_h).cuda()
     dC = torch.empty((n, n), device="cuda")
 
-    wplan = fmm.Plan(n, n, n, depth=args.depth, precision=args.precision, leaf_tile=args.leaf_tile, cutoff=4096)
+    wplan = fmm.Plan(n, n, n, depth=args.depth, precision=args.precision, leaf_tile=args.leaf_tile)
     depth = wplan.info["depth"]
     bn = wplan.info["leaf_tile"]
     step = lambda: wplan(dA, dB, dC)

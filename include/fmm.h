@@ -97,7 +97,7 @@ typedef struct {
 
 typedef struct fmm_plan_s* fmm_plan_t;
 
-/* Fill *opt with defaults: depth -1, cutoff 4096, leaf_tile 0, FP32, PAD,
+/* Fill *opt with defaults: depth -1, cutoff 2048, leaf_tile 0, FP32, PAD,
  * FIXED planner, Winograd, device operands.  Returns FMM_ERR_INVALID_ARG on NULL. */
 fmm_status_t fmm_options_default(fmm_options_t* opt);
 

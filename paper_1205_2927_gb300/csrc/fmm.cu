@@ -172,8 +172,8 @@ struct fmm_plan_s {
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
     size_t es16() const { return split_kind == kSplitTF32 ? 4 : 2; }
-    // depth >= 4: the last two levels of pre-additions (split-plane plans) and of
-    // post-additions run as one pass each; the middle level is never stored
+    // depth >= 4: the last three levels of pre-additions (split-plane plans) and
+    // of post-additions run as one pass each; the middle levels are never stored
     bool fuse_pre() const { return pre16 && depth >= 4; }
     bool fuse_post() const { return depth >= 4; }
     // depth 2: both levels at once from / into the caller's matrices
@@ -305,7 +305,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             const Level& C = p->lv[l + 1];
             L.full = (l < d - 1 || l == 0 || p->pre16) ? 1 : 0;
             const long long per = L.full ? 7 : 4;
-            if (p->fuse_pre() && l == d - 2) continue;   // written by neither pass: fused away
+            if (p->fuse_pre() && (l == d - 3 || l == d - 2)) continue;   // written by no pass: fused away
             if (p->fuse_root_pre() && l == 0) continue;   // fused away (both sides read the caller's operands)
             if (p->fuse_root_pre3() && l < d - 1) {   // fused away; B^T of the root instead
                 if (l == 0) p->bt_root = cv.take<float>((size_t)(p->N0 * p->K0));
@@ -323,7 +323,8 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
         const Level& Lf = p->lv[d];
         p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
         for (int l = 1; l < d; ++l) {
-            if ((p->fuse_post() || p->fuse_root_post()) && l == d - 1) continue;   // fused away
+            if (p->fuse_post() && (l == d - 1 || l == d - 2)) continue;   // fused away
+            if (p->fuse_root_post() && l == d - 1) continue;
             if (p->fuse_root_post3()) continue;
             Level& L = p->lv[l];
             L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
@@ -622,15 +623,15 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         View va{Pa.achild, L.k, L.m * L.k, L.m, L.k, L.m, L.k};
         View vb{Pa.bchild, L.k, L.n * L.k, L.n, L.k, L.n, L.k};
         const double in = 4.0 * (double)L.nodes * (double)(L.m * L.k + L.n * L.k);
-        if (p->fuse_pre() && l == d - 2) {
-            // levels d-2 and d-1 at once: level-(d-2) node operands -> the leaf operands
+        if (p->fuse_pre() && l == d - 3) {
+            // levels d-3 .. d-1 at once: level-(d-3) node operands -> the leaf operands
             const Level& Lf = lv[d];
-            Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 49};
-            Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 49};
-            FMM_CUDA(launch_pre_add2(va, L.nodes, sa, 0, kind, scale, stream));
-            FMM_CUDA(launch_pre_add2(vb, L.nodes, sb, 1, kind, scale, stream));
+            Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 343};
+            Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 343};
+            FMM_CUDA(launch_pre_add3(va, L.nodes, sa, 0, kind, scale, stream));
+            FMM_CUDA(launch_pre_add3(vb, L.nodes, sb, 1, kind, scale, stream));
             p->launches += 2;
-            p->acct[0] += in + 49.0 * (double)L.nodes * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
+            p->acct[0] += in + 343.0 * (double)L.nodes * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
             break;
         }
         if (p->pre16 && l == d - 1) {
@@ -757,14 +758,14 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
         return FMM_OK;
     }
     if (p->fuse_post()) {
-        // levels d-1 and d-2 at once: leaf products -> level-(d-2) node outputs
-        const Level& L = lv[d - 2];
+        // levels d-1 .. d-3 at once: leaf products -> level-(d-3) node outputs
+        const Level& L = lv[d - 3];
         const Level& Lf = lv[d];
-        FMM_CUDA(launch_post_add2(p->P, Lf.n, Lf.m * Lf.n, L.nodes, Lf.m, Lf.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
+        FMM_CUDA(launch_post_add3(p->P, Lf.n, Lf.m * Lf.n, L.nodes, Lf.m, Lf.n, L.cnode, L.n, L.m * L.n, -1, -1, 1.f,
                                   0.f, stream));
         p->launches += 1;
-        p->acct[1] += 4.0 * (double)L.nodes * (49.0 * (double)(Lf.m * Lf.n) + (double)(L.m * L.n));
-        top = d - 3;
+        p->acct[1] += 4.0 * (double)L.nodes * (343.0 * (double)(Lf.m * Lf.n) + (double)(L.m * L.n));
+        top = d - 4;
     }
     for (int l = top; l >= 0; --l) {
         const Level& L = lv[l];
@@ -1525,7 +1526,7 @@ fmm_status_t fmm_options_default(fmm_options_t* o) {
     if (!o) return FMM_ERR_INVALID_ARG;
     memset(o, 0, sizeof(*o));
     o->depth = -1;
-    o->cutoff = 4096;
+    o->cutoff = 2048;
     o->leaf_tile = 0;
     o->precision = FMM_PREC_FP32;
     o->odd = FMM_ODD_PAD;

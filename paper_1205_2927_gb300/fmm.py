@@ -97,7 +97,7 @@ def _check(status, where):
         raise FmmError(status, where)
 
 
-def options(depth=-1, cutoff=4096, leaf_tile=0, precision="fp32", odd="pad", planner="fixed",
+def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="pad", planner="fixed",
             algo="winograd", host_operands=0, refine_fp64=0) -> Options:
     o = Options()
     _check(_lib.fmm_options_default(C.byref(o)), "fmm_options_default")

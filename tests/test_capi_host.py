@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(F):
 
 def test_options_default(F):
     o = F.options()
-    assert (o.depth, o.cutoff, o.leaf_tile, o.precision, o.odd, o.planner, o.algo) == (-1, 4096, 0, 0, 0, 0, 0)
+    assert (o.depth, o.cutoff, o.leaf_tile, o.precision, o.odd, o.planner, o.algo) == (-1, 2048, 0, 0, 0, 0, 0)
 
 
 def test_status_strings(F):

@@ -70,12 +70,13 @@ def device_run(F, A, B, **kw):
 
 
 def test_square_16384_bench_configuration(F):
-    # the bench's default launch: fixed planner, cut-off 4096 -> depth 2, CTA-pair leaves
+    # the bench's default launch: fixed planner, default cut-off 2048 -> depth 3,
+    # CTA-pair leaves
     n = 16384
     A, B = I.operands(n, n, n, I.seed_for(2, 0))
-    C, info = device_run(F, A, B, precision="fp32", cutoff=4096)
-    assert (info["depth"], info["leaf_tile"]) == (2, 512)
-    check(A, B, C, sample_rows(n, 2, 1), FP32_BOUND, I.seed_for(2, 90))
+    C, info = device_run(F, A, B, precision="fp32")
+    assert (info["depth"], info["leaf_tile"]) == (3, 512)
+    check(A, B, C, sample_rows(n, 3, 1), FP32_BOUND, I.seed_for(2, 90))
 
 
 @pytest.mark.parametrize("odd", ["pad", "peel"])
