@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "single1024", "sweep", "split", "batched", "planner"],
+                    choices=["square", "single1024", "sweep", "large", "split", "batched", "planner"],
                     help="square: the headline line; the others measure the other configurations")
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -300,6 +300,37 @@ def wl_sweep(args):
             torch.cuda.empty_cache()
 
 
+def wl_large(args):
+    """n = 32768 (4.3 GB per matrix), U[-1,1], device-resident, depth 0 (classical) and the
+    deep plans where the additions' n^2 cost falls behind the leaves' n^3 work; CUDA-event
+    median of 3 calls after 2 warm-ups, error on sampled rows."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    n = 32768
+    A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(2, 5))
+    dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+    dC = torch.empty((n, n), device="cuda")
+    base = None
+    for d in (0, 3, 4):
+        p = fmm.Plan(n, n, n, depth=d)
+        p.profile(True)
+        ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 2)
+        prof = p.profile_read()
+        calls = max(prof["calls"], 1)
+        err = sampled_error(np, torch, dC, A_h, B_h, 8)
+        tile = p.info["leaf_tile"]
+        ws_gb = p.workspace.numel() / 1e9
+        p.close()
+        del p
+        torch.cuda.empty_cache()
+        base = ms if d == 0 else base
+        emit(args, {"workload": "large_n32768", "depth": d, "leaf_tile": tile, "ms": round(ms, 2),
+                    "gflops": round(2 * n ** 3 / ms / 1e6, 1), "speedup_vs_depth0": round(base / ms, 3),
+                    "pre_ms": round(prof["pre_ms"] / calls, 2), "leaf_ms": round(prof["leaf_ms"] / calls, 2),
+                    "post_ms": round(prof["post_ms"] / calls, 2), "workspace_gb": round(ws_gb, 1), "error": err})
+
+
 def wl_split(args):
     """Split-precision leaves: {fp32 (3xTF32), tf32, bf16x3, fp16x3} x depth 0..4 on
     19000x12000x15000 and 16384^3, entries N(0,1) and log-uniform [1e-3, 1e3]; error
@@ -421,7 +452,7 @@ def wl_planner(args):
                                                                            for k, v in s.items()}})
 
 
-WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "split": wl_split, "batched": wl_batched,
+WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "large": wl_large, "split": wl_split, "batched": wl_batched,
              "planner": wl_planner}
 
 def cublas_tf32_tflops(torch, n=8192, reps=10):
