@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "single1024", "sweep", "large", "split", "batched", "planner"],
+                    choices=["square", "single1024", "sweep", "large", "rmul", "split", "batched", "planner"],
                     help="square: the headline line; the others measure the other configurations")
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -331,6 +331,29 @@ def wl_large(args):
                     "post_ms": round(prof["post_ms"] / calls, 2), "workspace_gb": round(ws_gb, 1), "error": err})
 
 
+def wl_rmul(args):
+    """The classical quadrant recursion of Table 1 (RMUL, k-blocks accumulated in C)
+    against Winograd at the same depth, n = 16384, U[-1,1], device-resident, CUDA-event
+    median of 3 calls after 2 warm-ups; error on sampled rows."""
+    import numpy as np
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    n = 16384
+    A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(2, 0))
+    dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+    dC = torch.empty((n, n), device="cuda")
+    for algo in ("classical", "winograd"):
+        for d in (0, 1, 2, 3):
+            if algo == "winograd" and d == 0:
+                continue
+            p = fmm.Plan(n, n, n, depth=d, algo=algo)
+            ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 2)
+            err = sampled_error(np, torch, dC, A_h, B_h)
+            p.close()
+            emit(args, {"workload": "rmul_vs_winograd_n16384", "algo": algo, "depth": d, "ms": round(ms, 3),
+                        "gflops": round(2 * n ** 3 / ms / 1e6, 1), "error": err})
+
+
 def wl_split(args):
     """Split-precision leaves: {fp32 (3xTF32), tf32, bf16x3, fp16x3} x depth 0..4 on
     19000x12000x15000 and 16384^3, entries N(0,1) and log-uniform [1e-3, 1e3]; error
@@ -452,7 +475,8 @@ def wl_planner(args):
                                                                            for k, v in s.items()}})
 
 
-WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "large": wl_large, "split": wl_split, "batched": wl_batched,
+WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "large": wl_large, "rmul": wl_rmul, "split": wl_split,
+             "batched": wl_batched,
              "planner": wl_planner}
 
 def cublas_tf32_tflops(torch, n=8192, reps=10):

@@ -78,7 +78,14 @@ typedef enum {
 
 typedef enum {
     FMM_ALGO_WINOGRAD = 0,   /* 7-product Winograd recursion */
-    FMM_ALGO_CLASSICAL = 1   /* 8-product balanced quadrant recursion of Table 1 */
+    FMM_ALGO_CLASSICAL = 1   /* 8-product quadrant recursion of Table 1 (RMUL): C_ij = sum_k
+                                A_ik B_kj.  The independent (i, j) blocks share one leaf
+                                launch; the k-blocks (Eq. 1's halves of K per level, rounded
+                                up to 8 elements) are accumulated in order, the first with
+                                the caller's beta, the rest with beta = 1.  Depth 0 equals
+                                Winograd depth 0.  The fixed rule picks the depth; host-
+                                resident, batched and autotuned plans return
+                                FMM_ERR_UNSUPPORTED */
 } fmm_algo_t;
 
 typedef struct {

@@ -168,6 +168,7 @@ struct fmm_plan_s {
     int split_kind = 0;
     int pair = 0;        // leaves on CTA pairs (cta_group::2), 256 x 256 tiles
     int tile_req = 256;  // leaf tile the plan was made for (512: CTA pairs where the precision allows)
+    int rmul = 0;        // classical recursion (Table 1) depth; the Winograd depth is then 0
     void* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
@@ -366,7 +367,7 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL) return FMM_ERR_INVALID_ARG;
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
-    if (o->algo == FMM_ALGO_CLASSICAL) return FMM_ERR_UNSUPPORTED;
+    if (o->algo == FMM_ALGO_CLASSICAL && o->host_operands) return FMM_ERR_UNSUPPORTED;
     if (o->host_operands && o->odd != FMM_ODD_PAD) return FMM_ERR_UNSUPPORTED;
     return FMM_OK;
 }
@@ -444,67 +445,93 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int 
     return FMM_OK;
 }
 
+// K chunks of the classical recursion of Table 1 (RMUL) at depth d: every level
+// halves each chunk with Eq. 1's split (the first half takes the ceiling),
+// rounded up to a multiple of 8 elements so that each chunk's tile copies start
+// on 16 bytes.  The chunks are the k-blocks of C_ij = sum_k A_ik B_kj in the
+// recursion's order; depth 0 is one chunk.
+std::vector<std::pair<long long, long long>> rmul_chunks(long long K, int d) {
+    std::vector<std::pair<long long, long long>> c{{0, K}};
+    for (int l = 0; l < d; ++l) {
+        std::vector<std::pair<long long, long long>> n;
+        for (auto& [k0, len] : c) {
+            const long long h = std::min(len, rup((len + 1) / 2, 8));
+            n.push_back({k0, h});
+            n.push_back({k0 + h, len - h});
+        }
+        c.swap(n);
+    }
+    return c;
+}
+
+// Classical product: the operands are prepared once (split into hi / lo planes,
+// or B transposed for TF32), then one leaf launch per K chunk of the plan's
+// classical recursion: the first writes C = alpha A_0 B_0 + beta C, every later
+// one accumulates C += alpha A_s B_s (Table 1's C = AB, then C += AB leaves).
+// Depth 0 is the single-launch tensor-core GEMM.
 fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                            cudaStream_t stream) {
+    const int bf = p->split_kind;
+    const long long ld = p->ld16;
+    const float* Aop = A;
+    long long lda = p->lda;
     if (p->pre16) {
-        const int bf = p->split_kind;
         const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
-        const long long ld = p->ld16;
         Stack16 sa{p->a16[0], p->a16[1], ld, 0, 1};
         Stack16 sb{p->b16[0], p->b16[1], ld, 0, 1};
         FMM_CUDA(launch_split16(A, p->lda, p->M, p->K, sa, 0, bf, scale, 0, stream));
         FMM_CUDA(launch_split16(B, p->ldb, p->K, p->N, sb, 1, bf, scale, 1, stream));
         p->launches += 2;
         p->acct[0] += (double)(p->M * p->K + p->K * p->N) * (4.0 + 2.0 * p->es16());
-        mark(p, 1, stream);
+    } else {
+        FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
+        p->launches += 1;
+        p->acct[0] += 8.0 * (double)(p->K * p->N);
+        if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
+            FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
+            p->launches += 1;
+            p->acct[0] += 8.0 * (double)(p->M * p->K);
+            Aop = p->Acopy;
+            lda = p->ld_acopy;
+        }
+    }
+    mark(p, 1, stream);
+    bool first = true;
+    for (const auto& [k0, kc] : rmul_chunks(p->K, p->rmul)) {
+        if (kc <= 0) continue;
         GemmArgs args;
         memset(&args, 0, sizeof(args));
         fmm_status_t s;
-        for (int i = 0; i < 2; ++i) {
-            if ((s = encode_map16(&args.maps[i], p->a16[i], bf, p->K, p->M, 1, ld, p->M * ld, kBM)) != FMM_OK) return s;
-            if ((s = encode_map16(&args.maps[2 + i], p->b16[i], bf, p->K, p->N, 1, ld, p->N * ld,
-                                  p->pair ? 128 : p->bn)) != FMM_OK)
-                return s;
-        }
         GemmGroup& G = args.groups[0];
-        G.M = (int)p->M; G.N = (int)p->N; G.K = (int)p->K; G.batch = 1;
-        G.C = C; G.ldc = p->ldc; G.alpha = alpha; G.beta = beta;
-        G.map_a = 0; G.map_a_lo = 1; G.map_b = 2; G.map_b_lo = 3;
+        if (p->pre16) {
+            const size_t off = (size_t)k0 * p->es16();   // bytes; k0 is a multiple of 8
+            for (int i = 0; i < 2; ++i) {
+                if ((s = encode_map16(&args.maps[i], static_cast<char*>(p->a16[i]) + off, bf, kc, p->M, 1, ld,
+                                      p->M * ld, kBM)) != FMM_OK)
+                    return s;
+                if ((s = encode_map16(&args.maps[2 + i], static_cast<char*>(p->b16[i]) + off, bf, kc, p->N, 1, ld,
+                                      p->N * ld, p->pair ? 128 : p->bn)) != FMM_OK)
+                    return s;
+            }
+            G.map_a = 0; G.map_a_lo = 1; G.map_b = 2; G.map_b_lo = 3;
+        } else {
+            if ((s = encode_map(&args.maps[0], Aop + k0, kc, p->M, 1, lda, p->M * lda, kBM)) != FMM_OK) return s;
+            if ((s = encode_map(&args.maps[1], p->Bt + k0, kc, p->N, 1, p->ld_bt, p->N * p->ld_bt,
+                                p->pair ? 128 : p->bn)) != FMM_OK)
+                return s;
+            G.map_a = 0; G.map_b = 1;
+        }
+        G.M = (int)p->M; G.N = (int)p->N; G.K = (int)kc; G.batch = 1;
+        G.C = C; G.ldc = p->ldc; G.c_batch_stride = 0;
+        G.alpha = alpha; G.beta = first ? beta : 1.0f;
         G.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && p->ldc % 4 == 0) ? 1 : 0;
         args.num_groups = 1;
-        s = run_leaves(p, args, stream);
-        mark(p, 2, stream);
-        return s;
+        if ((s = run_leaves(p, args, stream)) != FMM_OK) return s;
+        if (!first) p->acct[1] += 8.0 * (double)(p->M * p->N);   // the accumulating launch reads and writes C
+        first = false;
     }
-    FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
-    p->launches += 1;
-    p->acct[0] += 8.0 * (double)(p->K * p->N);
-    const float* Aop = A;
-    long long lda = p->lda;
-    if ((reinterpret_cast<uintptr_t>(A) & 15) || (p->lda % 4)) {
-        FMM_CUDA(launch_copy2d(A, p->lda, p->M, p->K, p->Acopy, p->ld_acopy, stream));
-        p->launches += 1;
-        p->acct[0] += 8.0 * (double)(p->M * p->K);
-        Aop = p->Acopy;
-        lda = p->ld_acopy;
-    }
-    mark(p, 1, stream);
-    GemmArgs args;
-    memset(&args, 0, sizeof(args));
-    fmm_status_t s;
-    if ((s = encode_map(&args.maps[0], Aop, p->K, p->M, 1, lda, p->M * lda, kBM)) != FMM_OK) return s;
-    if ((s = encode_map(&args.maps[1], p->Bt, p->K, p->N, 1, p->ld_bt, p->N * p->ld_bt, p->pair ? 128 : p->bn)) != FMM_OK)
-        return s;
-    GemmGroup& G = args.groups[0];
-    G.M = (int)p->M; G.N = (int)p->N; G.K = (int)p->K; G.batch = 1;
-    G.C = C; G.ldc = p->ldc; G.c_batch_stride = 0;
-    G.alpha = alpha; G.beta = beta;
-    G.map_a = 0; G.map_b = 1;
-    G.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0 && p->ldc % 4 == 0) ? 1 : 0;
-    args.num_groups = 1;
-    fmm_status_t st = run_leaves(p, args, stream);
     mark(p, 2, stream);
-    return st;
+    return FMM_OK;
 }
 
 // Peeled border of a Winograd call on the even core (Mw x Kw x Nw), as classical
@@ -1020,7 +1047,8 @@ fmm_status_t batched_check(int count, const int64_t* M, const int64_t* N, const 
     if (opt) {
         fmm_status_t s = check_opts(opt);
         if (s != FMM_OK) return s;
-        if (opt->odd != FMM_ODD_PAD || opt->precision == FMM_PREC_FP16X3) return FMM_ERR_UNSUPPORTED;
+        if (opt->odd != FMM_ODD_PAD || opt->precision == FMM_PREC_FP16X3 || opt->algo == FMM_ALGO_CLASSICAL)
+            return FMM_ERR_UNSUPPORTED;
     }
     (void)A; (void)B; (void)C;
     return FMM_OK;
@@ -1037,6 +1065,11 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
     t.opt = o;
     t.host = o.host_operands ? 1 : 0;
     t.depth = (M == 0 || N == 0 || K == 0) ? 0 : depth;
+    t.rmul = 0;
+    if (o.algo == FMM_ALGO_CLASSICAL) {   // classical recursion: depth-0 operands, K chunks
+        t.rmul = t.depth;
+        t.depth = 0;
+    }
     t.peel = (o.odd == FMM_ODD_PEEL) ? 1 : 0;
     if (t.peel && t.depth > 0) {
         const long long g = 4LL << t.depth;
@@ -1322,8 +1355,13 @@ size_t scratch_bytes(long long M, long long N, long long K) {
 fmm_status_t plan_choose(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,
                          const fmm_options_t& o, void* ws, size_t ws_bytes, size_t* need, int& depth, int& bn,
                          cudaStream_t stream, bool query) {
-    if (o.planner == FMM_PLANNER_FIXED || M == 0 || N == 0 || K == 0) {
+    if (o.planner == FMM_PLANNER_FIXED || o.algo == FMM_ALGO_CLASSICAL || M == 0 || N == 0 || K == 0) {
         depth = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
+        if (o.algo == FMM_ALGO_CLASSICAL) {   // one launch spans all of C: tile by M, N
+            bn = o.leaf_tile ? o.leaf_tile : auto_tile(M, N, 0, o);
+            *need = plan_bytes(M, N, K, lda, ldb, ldc, o, depth, bn);
+            return FMM_OK;
+        }
         bn = o.leaf_tile ? o.leaf_tile : auto_tile(M, N, depth, o);
         *need = plan_bytes(M, N, K, lda, ldb, ldc, o, depth, bn);
         return FMM_OK;
@@ -1410,6 +1448,7 @@ fmm_status_t fmm_autotune(int64_t M, int64_t N, int64_t K, const fmm_options_t* 
     if (opt) o = *opt; else fmm_options_default(&o);
     fmm_status_t s = check_opts(&o);
     if (s != FMM_OK) return s;
+    if (o.algo == FMM_ALGO_CLASSICAL) return FMM_ERR_UNSUPPORTED;   // candidates are Winograd plans
     Cand c[16];
     const int n = candidates(M, N, K, o, c);
     size_t mx = 0;
@@ -1731,7 +1770,7 @@ fmm_status_t fmm_wait_selftest(fmm_plan_t p, int64_t limit_ns, fmm_stream_t stre
 
 fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precision, int* odd, int* algo) {
     if (!p) return FMM_ERR_INVALID_ARG;
-    if (depth) *depth = p->depth;
+    if (depth) *depth = p->rmul ? p->rmul : p->depth;
     if (leaf_tile) *leaf_tile = (p->pair || (p->host && p->tile_req == 512)) ? 512 : p->bn;
     if (precision) *precision = (int)p->opt.precision;
     if (odd) *odd = (int)p->opt.odd;

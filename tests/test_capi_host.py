@@ -140,3 +140,15 @@ def test_exhaustive_query_includes_scratch(F):
     fixed = _query(F, 2048, 2048, 2048, planner="fixed", depth=1)
     ex = _query(F, 2048, 2048, 2048, planner="exhaustive")
     assert ex > fixed + 3 * 2048 * 2048 * 4 - 1
+
+
+def test_classical_recursion_options(F):
+    # Table 1's recursion reuses the depth-0 operands: the same workspace at every depth
+    n = 2048
+    sizes = [_query(F, n, n, n, depth=d, algo="classical") for d in range(4)]
+    assert sizes[0] == _query(F, n, n, n, depth=0)
+    assert len(set(sizes)) == 1
+    need = C.c_size_t(0)
+    lib = F.library()
+    o = F.options(algo="classical", host_operands=1)
+    assert lib.fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 6

@@ -389,3 +389,32 @@ def test_wait_timeout_is_reported_and_context_stays_usable(fmm):
     ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
     assert np.array_equal(dC.cpu().numpy(), ref)
     p.close()
+
+
+# --- classical recursion of Table 1 (RMUL): k-blocks accumulated in C -------------
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("m,k,n,d", [(300, 200, 260, 1), (512, 512, 512, 2), (777, 333, 515, 3), (130, 5, 90, 3),
+                                     (64, 1, 64, 2)])
+def test_rmul_bit_exact_small_int(fmm, prec, m, k, n, d):
+    A = I.small_int((m, k), 18000 + m + d, r=2)
+    B = I.small_int((k, n), 18100 + n + d, r=2)
+    C, info = run(fmm, A, B, depth=d, precision=prec, algo="classical")
+    assert (info["depth"], info["algo"]) == (d, 1)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64))
+    assert np.array_equal(O.rmul(A.astype(np.int64), B.astype(np.int64), d), ref)
+    assert np.array_equal(C, ref.astype(np.float32))
+
+
+def test_rmul_float_and_blas(fmm):
+    n = 1024
+    A, B = I.operands(n, n, n, I.seed_for(1, 23), "normal")
+    C0 = I.uniform((n, n), 19)
+    for d in (1, 3):
+        C, _ = run(fmm, A, B, C0, alpha=0.5, beta=-2.0, depth=d, algo="classical")
+        ref = O.gemm(0.5, A, B, -2.0, C0)
+        assert np.max(np.abs(C - ref)) / (np.abs(A).max() * np.abs(B).max() * n) <= FP32_BOUND
+    # beta is applied once, then the later k-blocks accumulate: a NaN-filled C with beta = 0 stays clean
+    C, _ = run(fmm, A, B, np.full((n, n), np.nan, np.float32), beta=0.0, depth=2, algo="classical")
+    assert np.all(np.isfinite(C))
+    assert O.error_metric(C, O.classical(A, B), A, B) <= FP32_BOUND
