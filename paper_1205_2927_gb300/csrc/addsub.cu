@@ -880,11 +880,15 @@ __global__ void __launch_bounds__(128, 2) post_add3_kernel(const float* __restri
     }
 }
 
-// Split jobs of a batched launch (one 32 x 32 tile per block, jobs found by
-// binary search on their first tile).
+// Split jobs of a batched launch: one 32 x 128 block of the source per CTA
+// (jobs found by binary search on their first block).  Every thread issues all
+// of its loads before its first store.  Untransposed jobs go straight from
+// 16-byte loads to the planes (a warp covers 512 contiguous bytes of a row);
+// transposed jobs stage the block in a 32 x 129 shared tile (conflict-free both
+// ways) and leave it as 128 rows of 32 elements.
 template <int KIND>
 __global__ void __launch_bounds__(256) batched_split_kernel(const SplitJob* __restrict__ jobs, int njobs) {
-    __shared__ float tile[32][33];
+    __shared__ float tile[32][129];
     const long long t = blockIdx.x;
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
@@ -893,26 +897,61 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const SplitJob* __re
     }
     const SplitJob J = jobs[lo];
     const long long local = t - J.tile_begin;
-    const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 128;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (!J.transpose) {
+        const bool vec = (reinterpret_cast<uintptr_t>(J.src) & 15) == 0 && (J.lds & 3) == 0;
+        float4 v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long long r = r0 + ty + 8 * i, c = c0 + tx;
-        tile[ty + 8 * i][tx] = (r < J.rows && c < J.cols) ? J.src[r * J.lds + c] : 0.0f;
+        for (int j = 0; j < 4; ++j) {
+            const int g = tid + 256 * j;   // row g / 32 of the block, columns 4 (g % 32) .. + 3
+            const long long r = r0 + (g >> 5), c = c0 + 4 * (g & 31);
+            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r >= J.rows || c >= J.cols) continue;
+            const float* src = J.src + r * J.lds + c;
+            if (vec && c + 3 < J.cols) {
+                v[j] = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+                v[j].x = __ldg(src);
+                if (c + 1 < J.cols) v[j].y = __ldg(src + 1);
+                if (c + 2 < J.cols) v[j].z = __ldg(src + 2);
+                if (c + 3 < J.cols) v[j].w = __ldg(src + 3);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int g = tid + 256 * j;
+            const long long r = r0 + (g >> 5), c = c0 + 4 * (g & 31);
+            // ld is a multiple of 8, so a group of 4 never crosses a row: padding columns get zeros
+            if (r < J.rows && c < J.cols) split_store<KIND>(J.dst, J.lo, r * J.ldd + c, v[j], 1.0f);
+        }
+        return;
     }
+    // source rows r0 + i (i = warp + 8 s), columns c0 + lane + 32 q
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    float x[4][4];
+#pragma unroll
+    for (int sI = 0; sI < 4; ++sI)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long long r = r0 + warp + 8 * sI, c = c0 + lane + 32 * q;
+            x[sI][q] = (r < J.rows && c < J.cols) ? __ldg(J.src + r * J.lds + c) : 0.0f;
+        }
+#pragma unroll
+    for (int sI = 0; sI < 4; ++sI)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tile[warp + 8 * sI][lane + 32 * q] = x[sI][q];
     __syncthreads();
-    const int u = ty * 32 + tx;
-    const int a = u >> 3, q = (u & 7) * 4;
-    float4 v;
-    long long orow, ocol, lim_r, lim_c;
-    if (J.transpose) {
-        v = make_float4(tile[q][a], tile[q + 1][a], tile[q + 2][a], tile[q + 3][a]);
-        orow = c0 + a; ocol = r0 + q; lim_r = J.cols; lim_c = J.rows;
-    } else {
-        v = make_float4(tile[a][q], tile[a][q + 1], tile[a][q + 2], tile[a][q + 3]);
-        orow = r0 + a; ocol = c0 + q; lim_r = J.rows; lim_c = J.cols;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int g = tid + 256 * j;   // output row a (a source column), 4 consecutive output columns
+        const int a = g >> 3, q = (g & 7) * 4;
+        const long long orow = c0 + a, ocol = r0 + q;
+        if (orow < J.cols && ocol < J.rows) {
+            const float4 v = make_float4(tile[q][a], tile[q + 1][a], tile[q + 2][a], tile[q + 3][a]);
+            split_store<KIND>(J.dst, J.lo, orow * J.ldd + ocol, v, 1.0f);
+        }
     }
-    if (orow < lim_r && ocol < lim_c) split_store<KIND>(J.dst, J.lo, orow * J.ldd + ocol, v, 1.0f);
 }
 
 inline unsigned gy(long long rows) { return (unsigned)(rows < 65535 ? (rows > 0 ? rows : 1) : 65535); }

@@ -930,8 +930,8 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             void* bh = cv.take<char>((size_t)N[i] * ld * es);
             void* bl = cv.take<char>((size_t)N[i] * ld * es);
             if (!ws) continue;
-            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], ah, al, ld, 0, (int)((K[i] + 31) / 32), 0});
-            sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 31) / 32), 1});
+            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], ah, al, ld, 0, (int)((K[i] + 127) / 128), 0});
+            sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 127) / 128), 1});
             fmm_status_t s;
             const int kd = b->split_kind;
             if ((s = encode_map16(&maps[nm], ah, kd, K[i], M[i], 1, ld, M[i] * ld, kBM)) != FMM_OK) return s;

@@ -129,8 +129,8 @@ struct SplitJob {
     void* dst;
     void* lo;
     long long ldd;
-    long long tile_begin;
-    int tiles_c;
+    long long tile_begin;   // first 32 x 128 block of the job in the launch
+    int tiles_c;            // 128-column blocks per 32-row band of the source
     int transpose;
 };
 cudaError_t launch_batched_split(const SplitJob* jobs, int njobs, long long total_tiles, int kind,

@@ -94,10 +94,13 @@ def register(params, mean, std):
     fmm.fmm_set_cost_model(params, mean, std)
 
 
-def choice(M, N, K, planner, precision="fp32", cutoff=1024):
-    """(depth, tile) the library's planner picks for a shape (no timing)."""
+def choice(M, N, K, planner, precision="fp32", cutoff=None):
+    """(depth, tile) the library's planner picks for a shape (no timing);
+    cutoff None = the library's default."""
     import torch
-    q = fmm.options(planner=planner, precision=precision, cutoff=cutoff)
+    q = fmm.options(planner=planner, precision=precision)
+    if cutoff is not None:
+        q.cutoff = int(cutoff)
     _, need = fmm.fmm_plan(M, N, K, K, N, N, q, query_only=True)
     ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
     h, _ = fmm.fmm_plan(M, N, K, K, N, N, q, ws.data_ptr(), ws.numel())
@@ -106,9 +109,10 @@ def choice(M, N, K, planner, precision="fp32", cutoff=1024):
     return info["depth"], info["leaf_tile"]
 
 
-def evaluate(recs, precision="fp32", cutoff=1024):
+def evaluate(recs, precision="fp32", cutoff=None):
     """For every shape in `recs` (all candidates timed): time of the MLP's pick,
-    of the fixed planner's pick and of the best candidate."""
+    of the fixed planner's pick (at the library's default cut-off unless given)
+    and of the best candidate."""
     by_shape = {}
     for r in recs:
         by_shape.setdefault((r["M"], r["K"], r["N"]), {})[(r["depth"], r["tile"])] = r["ms"]
