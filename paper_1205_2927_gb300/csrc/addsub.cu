@@ -222,19 +222,25 @@ __global__ void __launch_bounds__(128) post_add_kernel(const float* __restrict__
 __global__ void __launch_bounds__(256) transpose_kernel(const float* __restrict__ B, long long ldb, long long K,
                                                         long long N, float* __restrict__ Bt, long long ldt,
                                                         long long rows_out, long long cols_out) {
-    __shared__ float tile[32][33];
-    const long long k0 = (long long)blockIdx.y * 32, n0 = (long long)blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    // one 128 (k) x 32 (n) block of B per CTA: 16 loads in flight per thread,
+    // then 32 rows of B^T written as 512 contiguous bytes each
+    __shared__ float tile[32][129];   // [n][k]
+    const long long k0 = (long long)blockIdx.y * 128, n0 = (long long)blockIdx.x * 32;
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
+    float x[16];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long long k = k0 + ty + 8 * i, n = n0 + tx;
-        tile[ty + 8 * i][tx] = (k < K && n < N) ? B[k * ldb + n] : 0.0f;
+    for (int i = 0; i < 16; ++i) {
+        const long long k = k0 + warp + 8 * i, n = n0 + lane;
+        x[i] = (k < K && n < N) ? __ldg(B + k * ldb + n) : 0.0f;
     }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tile[lane][warp + 8 * i] = x[i];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long long n = n0 + ty + 8 * i, k = k0 + tx;
-        if (n < rows_out && k < cols_out) Bt[n * ldt + k] = tile[tx][ty + 8 * i];
+    for (int j = 0; j < 16; ++j) {
+        const int v = tid + 256 * j;   // row v / 128 of the B^T block, column v % 128
+        const long long n = n0 + (v >> 7), k = k0 + (v & 127);
+        if (n < rows_out && k < cols_out) Bt[n * ldt + k] = tile[v >> 7][v & 127];
     }
 }
 
@@ -497,35 +503,66 @@ __global__ void __launch_bounds__(256) pre_add16_b_root_kernel(const float* __re
 }
 
 // Plain split (transpose = 0: rows x cols -> rows x ld planes) or transposed
-// split (transpose = 1: X is rows(K) x cols(N), planes are cols x ld).
+// split (transpose = 1: X is rows(K) x cols(N), planes are cols x ld).  Every
+// thread issues all of its loads before its first store.  Plain: one 32 x 128
+// block per CTA, 16-byte loads straight to the planes.  Transposed: one
+// 128 (row) x 32 (column) block staged in a shared tile, left as 32 plane rows
+// of 128 elements (512 contiguous bytes each).
 template <int KIND, bool TRANS>
 __global__ void __launch_bounds__(256) split16_kernel(const float* __restrict__ X, long long ldx, long long rows,
                                                       long long cols, Stack16 out, const float* __restrict__ scale,
                                                       int which) {
-    __shared__ float tile[32][33];
     const float sc = scale ? scale[which] : 1.0f;
-    const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
+    if (!TRANS) {
+        const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 128;
+        const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ldx & 3) == 0;
+        float4 v[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long long r = r0 + ty + 8 * i, c = c0 + tx;
-        tile[ty + 8 * i][tx] = (r < rows && c < cols) ? X[r * ldx + c] : 0.0f;
+        for (int j = 0; j < 4; ++j) {
+            const int g = tid + 256 * j;   // row g / 32 of the block, columns 4 (g % 32) .. + 3
+            const long long r = r0 + (g >> 5), c = c0 + 4 * (g & 31);
+            v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r >= rows || c >= cols) continue;
+            const float* src = X + r * ldx + c;
+            if (vec && c + 3 < cols) {
+                v[j] = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+                v[j].x = __ldg(src);
+                if (c + 1 < cols) v[j].y = __ldg(src + 1);
+                if (c + 2 < cols) v[j].z = __ldg(src + 2);
+                if (c + 3 < cols) v[j].w = __ldg(src + 3);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int g = tid + 256 * j;
+            const long long r = r0 + (g >> 5), c = c0 + 4 * (g & 31);
+            // ld is a multiple of 8, so a group of 4 never crosses a row: padding columns get zeros
+            if (r < rows && c < cols) split_store<KIND>(out.hi, out.lo, r * out.ld + c, v[j], sc);
+        }
+        return;
     }
+    __shared__ float tile[32][129];   // [column of X][row of X]
+    const long long r0 = (long long)blockIdx.y * 128, c0 = (long long)blockIdx.x * 32;
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const long long r = r0 + warp + 8 * i, c = c0 + lane;
+        x[i] = (r < rows && c < cols) ? __ldg(X + r * ldx + c) : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tile[lane][warp + 8 * i] = x[i];
     __syncthreads();
-    const int t = ty * 32 + tx;
-    const int a = t >> 3, q = (t & 7) * 4;   // output row a of the tile, 4 consecutive output columns
-    float4 v;
-    long long orow, ocol, olim_r, olim_c;
-    if (TRANS) {   // output (c, r): row = column of X
-        v = make_float4(tile[q][a], tile[q + 1][a], tile[q + 2][a], tile[q + 3][a]);
-        orow = c0 + a; ocol = r0 + q; olim_r = cols; olim_c = rows;
-    } else {
-        v = make_float4(tile[a][q], tile[a][q + 1], tile[a][q + 2], tile[a][q + 3]);
-        orow = r0 + a; ocol = c0 + q; olim_r = rows; olim_c = cols;
-    }
-    if (orow < olim_r && ocol < olim_c) {
-        // ld is a multiple of 8, so a group of 4 never crosses a row: padding columns get zeros
-        split_store<KIND>(out.hi, out.lo, orow * out.ld + ocol, v, sc);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int g = tid + 256 * j;   // plane row g / 32 (a column of X), 4 consecutive plane columns
+        const int a = g >> 5, q = (g & 31) * 4;
+        const long long orow = c0 + a, ocol = r0 + q;
+        if (orow < cols && ocol < rows) {
+            const float4 v = make_float4(tile[a][q], tile[a][q + 1], tile[a][q + 2], tile[a][q + 3]);
+            split_store<KIND>(out.hi, out.lo, orow * out.ld + ocol, v, sc);
+        }
     }
 }
 
@@ -1011,7 +1048,7 @@ cudaError_t launch_transpose(const float* B, long long ldb, long long K, long lo
     if (rows_out < 0) rows_out = N;
     if (cols_out < 0) cols_out = K;
     if (rows_out <= 0 || cols_out <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((rows_out + 31) / 32), (unsigned)((cols_out + 31) / 32));
+    dim3 grid((unsigned)((rows_out + 31) / 32), (unsigned)((cols_out + 127) / 128));
     transpose_kernel<<<grid, dim3(32, 8), 0, stream>>>(B, ldb, K, N, Bt, ldt, rows_out, cols_out);
     return cudaGetLastError();
 }
@@ -1103,7 +1140,9 @@ cudaError_t launch_pre_add16_b_root(const float* B, long long ldb, long long K, 
 cudaError_t launch_split16(const float* X, long long ldx, long long rows, long long cols, const Stack16& out,
                            int transpose, int kind, const float* scale, int which, cudaStream_t stream) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    // plain: 32 x 128 blocks; transposed: 128 (row) x 32 (column) blocks
+    const dim3 grid = transpose ? dim3((unsigned)((cols + 31) / 32), (unsigned)((rows + 127) / 128))
+                                : dim3((unsigned)((cols + 127) / 128), (unsigned)((rows + 31) / 32));
 #define FMM_SPLIT(K, T) split16_kernel<K, T><<<grid, dim3(32, 8), 0, stream>>>(X, ldx, rows, cols, out, scale, which)
 #define FMM_SPLITK(T)                                   \
     switch (kind) {                                      \
