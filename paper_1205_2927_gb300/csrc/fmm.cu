@@ -169,6 +169,7 @@ struct fmm_plan_s {
     int pair = 0;        // leaves on CTA pairs (cta_group::2), 256 x 256 tiles
     int tile_req = 256;  // leaf tile the plan was made for (512: CTA pairs where the precision allows)
     int rmul = 0;        // classical recursion (Table 1) depth; the Winograd depth is then 0
+    char* tile_sched = nullptr;   // pair plans: dynamic tile order (counter + per-pair rings)
     void* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
     void* b16[2] = {};   // hi, lo planes of the leaf B^T operands
     long long ld16 = 0;
@@ -240,6 +241,7 @@ void make_child(const fmm_plan_s* p, fmm_plan_s& c);
 void layout(fmm_plan_s* p, char* ws, size_t* needed) {
     Carver cv(ws);
     p->status = cv.take<unsigned>(64);
+    if (p->pair && !p->host) p->tile_sched = cv.take<char>(kTileSchedBytes);
     const int d = p->depth;
     if (p->host) {
         // device copies of the root quadrants; the children run on these
@@ -421,6 +423,11 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int 
         args.ext_maps = nullptr;
         args.ext_groups = nullptr;
         args.status = p->status;
+        if (p->tile_sched) {   // dynamic tile order: counter and rings start from zero
+            FMM_CUDA(cudaMemsetAsync(p->tile_sched, 0, kTileSchedBytes, stream));
+            args.tile_counter = reinterpret_cast<int*>(p->tile_sched);
+            args.tile_seq = reinterpret_cast<unsigned long long*>(p->tile_sched + 256);
+        }
         FMM_CUDA(launch_leaf_gemm_pair(args, mode, p->num_sms, stream));
         p->launches += args.total_tiles > 0 ? 1 : 0;
         return FMM_OK;

@@ -94,6 +94,39 @@ __device__ __forceinline__ void decode_tile(const GemmGroup* groups, int ng, int
     tm = sr * raster_m + (rr - tn * gm);
 }
 
+// Dynamic tile order of a CTA-pair launch.  CTA 0's producer takes tiles from
+// the launch-wide counter and publishes the pair's i-th tile in slot i of the
+// pair's ring; every other role of the pair (CTA 0's MMA and epilogue warps,
+// CTA 1's producer and epilogue warps) reads the same sequence, so all of them
+// walk the same tiles while the pairs together stay on neighbouring tiles
+// (operand panels shared in L2) however their speeds drift.
+__device__ __forceinline__ void seq_publish(unsigned long long* slot, unsigned i, long long t) {
+    const unsigned long long v = ((unsigned long long)(i + 1) << 32) | (unsigned long long)(unsigned)t;
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(slot), "l"(v) : "memory");
+}
+// The pair's i-th tile, or -1 when the block is aborting or the bounded wait ran
+// out (then the status word and the block's abort flag are set).
+__device__ __forceinline__ long long seq_read(const unsigned long long* slot, unsigned i, volatile int* abort_flag,
+                                              unsigned* status) {
+    const unsigned long long want = (unsigned long long)(i + 1);
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(slot) : "memory");
+        if ((v >> 32) == want) return (long long)(unsigned)(v & 0xffffffffull);
+        if ((it & 63u) == 0) {
+            if (*abort_flag) return -1;
+            const unsigned long long now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > FMM_WAIT_LIMIT_NS) {
+                atomicOr(status, FMM_DEV_TIMEOUT_BIT);
+                *abort_flag = 1;
+                return -1;
+            }
+        }
+    }
+}
+
 template <int BN, int MODE>
 __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kernel(const __grid_constant__ GemmArgs args) {
     using Cfg = LeafCfg<BN, MODE>;
@@ -458,6 +491,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     const long long total = args.total_tiles;   // 256 x 256 pair tiles
     const long long pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
     unsigned* status = args.status;
+    const bool dyn = args.tile_counter != nullptr;   // dynamic tile order (the pair's ring)
+    unsigned long long* seq = dyn ? args.tile_seq + pair * kPairSeqSlots : nullptr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::kStages; ++s) {
@@ -488,7 +523,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
             uint32_t phase = 0;
             bool ok = true;
             long long issued = 0;
-            for (long long t = pair; t < total && ok; t += npairs) {
+            long long t_next = (dyn && rank == 0) ? (long long)atomicAdd(args.tile_counter, 1) : 0;
+            for (unsigned i = 0; ok; ++i) {
+                long long t;
+                if (!dyn) {
+                    t = pair + (long long)i * npairs;
+                } else if (rank == 0) {   // take the next tile (one ahead) and publish it
+                    t = t_next;
+                    seq_publish(seq + (i % kPairSeqSlots), i, t < total ? t : total);
+                    if (t < total) t_next = atomicAdd(args.tile_counter, 1);
+                } else {
+                    t = seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status);
+                    if (t < 0) { ok = false; break; }
+                }
+                if (t >= total) break;
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const GemmGroup& G = groups[g];
@@ -533,7 +581,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (long long t = pair; t < total && ok; t += npairs) {
+            for (unsigned i = 0; ok; ++i) {
+                const long long t = dyn ? seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status)
+                                        : pair + (long long)i * npairs;
+                if (t < 0 || t >= total) break;
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
@@ -588,7 +639,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         const int q = warp & 3;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (long long t = pair; t < total; t += npairs) {
+        for (unsigned i = 0;; ++i) {
+            long long t = pair + (long long)i * npairs;
+            if (dyn) {
+                if (lane == 0) t = seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status);
+                t = __shfl_sync(0xffffffffu, t, 0);
+            }
+            if (t < 0 || t >= total) break;
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
             const GemmGroup& G = groups[g];
@@ -693,7 +750,8 @@ static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStrea
         }
         max_clusters[dev] = n < num_sms / 2 ? n : num_sms / 2;
     }
-    const long long cap = (dev >= 0 && dev < 64) ? max_clusters[dev] : num_sms / 2;
+    long long cap = (dev >= 0 && dev < 64) ? max_clusters[dev] : num_sms / 2;
+    if (args.tile_counter && cap > kMaxPairs) cap = kMaxPairs;   // the rings hold kMaxPairs pairs
     if (args.total_tiles <= 0) return cudaSuccess;
     const long long pairs = args.total_tiles < cap ? args.total_tiles : cap;
     kern<<<(unsigned)(2 * pairs), Cfg::kThreads, Cfg::kSmem, stream>>>(args);
