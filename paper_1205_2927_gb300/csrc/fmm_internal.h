@@ -43,15 +43,16 @@ struct GemmArgs {
     int raster_m;                  // tile rows per raster band
     long long total_tiles;
     unsigned* status;              // device status word
-    // dynamic tile order of a CTA-pair launch (null: static round robin): the
-    // next free tile (zero before the launch), and each pair's ring of
-    // kPairSeqSlots 64-bit slots ((index + 1) << 32 | tile; zero before the launch)
+    // dynamic tile order of a leaf launch (null: static round robin): the next
+    // free tile (zero before the launch), and one ring per CTA (per pair for
+    // CTA-pair launches) of kPairSeqSlots 64-bit slots ((index + 1) << 32 | tile;
+    // zero before the launch)
     int* tile_counter;
     unsigned long long* tile_seq;
 };
-constexpr int kPairSeqSlots = 64;     // ring slots per pair (its roles stay within ~10 tiles)
-constexpr int kMaxPairs = 128;        // pairs a dynamically scheduled launch may use
-constexpr size_t kTileSchedBytes = 256 + (size_t)kMaxPairs * kPairSeqSlots * 8;   // counter, then the rings
+constexpr int kPairSeqSlots = 64;     // ring slots per CTA / pair (its roles stay within ~10 tiles)
+constexpr int kMaxSeqRings = 256;     // CTAs / pairs a dynamically scheduled launch may use
+constexpr size_t kTileSchedBytes = 256 + (size_t)kMaxSeqRings * kPairSeqSlots * 8;   // counter, then the rings
 
 // precision of a leaf launch
 // kLeafBF16x3 / kLeafFP16x3 split fp32 tiles in shared memory; the *P modes

@@ -94,12 +94,13 @@ __device__ __forceinline__ void decode_tile(const GemmGroup* groups, int ng, int
     tm = sr * raster_m + (rr - tn * gm);
 }
 
-// Dynamic tile order of a CTA-pair launch.  CTA 0's producer takes tiles from
-// the launch-wide counter and publishes the pair's i-th tile in slot i of the
-// pair's ring; every other role of the pair (CTA 0's MMA and epilogue warps,
-// CTA 1's producer and epilogue warps) reads the same sequence, so all of them
-// walk the same tiles while the pairs together stay on neighbouring tiles
-// (operand panels shared in L2) however their speeds drift.
+// Dynamic tile order of a leaf launch.  The producer (CTA 0's, for a CTA pair)
+// takes tiles from the launch-wide counter and publishes its i-th tile in slot i
+// of its ring; every other role (MMA issuer, epilogue and split warps, and the
+// peer CTA's producer and epilogue warps of a pair) reads the same sequence, so
+// all of them walk the same tiles while the CTAs together stay on neighbouring
+// tiles (operand panels shared in L2) however their speeds drift, and uneven
+// tiles (a batched launch) balance as they are taken.
 __device__ __forceinline__ void seq_publish(unsigned long long* slot, unsigned i, long long t) {
     const unsigned long long v = ((unsigned long long)(i + 1) << 32) | (unsigned long long)(unsigned)t;
     asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(slot), "l"(v) : "memory");
@@ -153,6 +154,8 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
     const int ng = args.num_groups;
     const long long total = args.total_tiles;
     unsigned* status = args.status;
+    const bool dyn = args.tile_counter != nullptr;   // dynamic tile order (this CTA's ring)
+    unsigned long long* seq = dyn ? args.tile_seq + (long long)blockIdx.x * kPairSeqSlots : nullptr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::kStages; ++s) {
@@ -183,7 +186,15 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             uint32_t phase = 0;
             bool ok = true;
             long long issued = 0;
-            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            long long t_next = dyn ? (long long)atomicAdd(args.tile_counter, 1) : 0;
+            for (unsigned i = 0; ok; ++i) {
+                long long t = blockIdx.x + (long long)i * gridDim.x;
+                if (dyn) {   // take the next tile (one ahead) and publish it to this CTA's roles
+                    t = t_next;
+                    seq_publish(seq + (i % kPairSeqSlots), i, t < total ? t : total);
+                    if (t < total) t_next = atomicAdd(args.tile_counter, 1);
+                }
+                if (t >= total) break;
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const GemmGroup& G = groups[g];
@@ -222,7 +233,10 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            for (unsigned i = 0; ok; ++i) {
+                const long long t = dyn ? seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status)
+                                        : blockIdx.x + (long long)i * gridDim.x;
+                if (t < 0 || t >= total) break;
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
@@ -298,7 +312,13 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
         const int q = warp & 3;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        for (unsigned i = 0;; ++i) {
+            long long t = blockIdx.x + (long long)i * gridDim.x;
+            if (dyn) {
+                if (lane == 0) t = seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status);
+                t = __shfl_sync(0xffffffffu, t, 0);
+            }
+            if (t < 0 || t >= total) break;
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
             const GemmGroup& G = groups[g];
@@ -361,7 +381,13 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        for (unsigned i = 0; ok; ++i) {
+            long long t = blockIdx.x + (long long)i * gridDim.x;
+            if (dyn) {
+                if (lane == 0) t = seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status);
+                t = __shfl_sync(0xffffffffu, t, 0);
+            }
+            if (t < 0 || t >= total) break;
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
             const GemmGroup& G = groups[g];
@@ -399,7 +425,13 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        for (unsigned i = 0; ok; ++i) {
+            long long t = blockIdx.x + (long long)i * gridDim.x;
+            if (dyn) {
+                if (lane == 0) t = seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status);
+                t = __shfl_sync(0xffffffffu, t, 0);
+            }
+            if (t < 0 || t >= total) break;
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
             const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
@@ -751,7 +783,7 @@ static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStrea
         max_clusters[dev] = n < num_sms / 2 ? n : num_sms / 2;
     }
     long long cap = (dev >= 0 && dev < 64) ? max_clusters[dev] : num_sms / 2;
-    if (args.tile_counter && cap > kMaxPairs) cap = kMaxPairs;   // the rings hold kMaxPairs pairs
+    if (args.tile_counter && cap > kMaxSeqRings) cap = kMaxSeqRings;   // one ring per pair
     if (args.total_tiles <= 0) return cudaSuccess;
     const long long pairs = args.total_tiles < cap ? args.total_tiles : cap;
     kern<<<(unsigned)(2 * pairs), Cfg::kThreads, Cfg::kSmem, stream>>>(args);
@@ -784,7 +816,8 @@ static cudaError_t launch_impl(const GemmArgs& args, int num_sms, cudaStream_t s
         if (dev >= 0 && dev < 64) attr_done[dev] = true;
     }
     if (args.total_tiles <= 0) return cudaSuccess;
-    const long long grid = args.total_tiles < num_sms ? args.total_tiles : num_sms;
+    long long grid = args.total_tiles < num_sms ? args.total_tiles : num_sms;
+    if (args.tile_counter && grid > kMaxSeqRings) grid = kMaxSeqRings;   // one ring per CTA
     kern<<<(unsigned)grid, Cfg::kThreads, Cfg::kSmem, stream>>>(args);
     return cudaGetLastError();
 }
