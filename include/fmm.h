@@ -125,9 +125,13 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K,
 /* Run the plan: C <- alpha * A * B + beta * C.  A, B, C are device pointers,
  * or pinned host pointers when the plan was made with host_operands = 1 (then
  * the call streams A and B in and C out on internal copy streams ordered
- * after `stream`, and returns once C is back in host memory).  Pageable host
- * memory is rejected with FMM_ERR_INVALID_ARG.  Asynchronous for device
- * operands. */
+ * after `stream`; C is complete in host memory once `stream` has reached this
+ * point, e.g. after cudaStreamSynchronize(stream)).  Pageable host memory is
+ * rejected with FMM_ERR_INVALID_ARG.  Asynchronous in both cases.
+ * A plan serves one call at a time: calls on one stream are ordered by the
+ * stream; calls of one plan on different streams must be ordered by the
+ * caller, since they share the plan's workspace temporaries and its
+ * tile-scheduling area. */
 fmm_status_t fmm_gemm(fmm_plan_t plan, float alpha, const float* A, const float* B,
                       float beta, float* C, fmm_stream_t stream);
 
