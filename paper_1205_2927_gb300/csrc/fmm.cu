@@ -120,21 +120,24 @@ fmm_status_t encode_map(CUtensorMap* map, const float* base, long long cols, lon
 
 // 3-D K-major tile map of a split plane: 64-byte rows (32 16-bit or 16 fp32
 // elements of K), box {row, box_rows, 1}, 64-byte swizzle.
+// Tensor map over split planes: wide = the CTA-pair kernel's 128-byte box rows
+// with 128-byte swizzle, else the single-CTA kernel's 64-byte rows with 64-byte
+// swizzle.
 fmm_status_t encode_map16(CUtensorMap* map, const void* base, int kind, long long cols, long long rows,
-                          long long batch, long long ld, long long batch_stride, int box_rows) {
+                          long long batch, long long ld, long long batch_stride, int box_rows, bool wide = false) {
     if (cols <= 0 || rows <= 0 || batch <= 0) return FMM_ERR_INVALID_ARG;
     const long long es = kind == kSplitTF32 ? 4 : 2;
     if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * es) % 16 || (batch_stride * es) % 16) return FMM_ERR_ALIGNMENT;
     cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
     cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(batch_stride * es)};
-    cuuint32_t box[3] = {(cuuint32_t)(64 / es), (cuuint32_t)box_rows, 1u};
+    cuuint32_t box[3] = {(cuuint32_t)((wide ? 128 : 64) / es), (cuuint32_t)box_rows, 1u};
     cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUtensorMapDataType dt = kind == kSplitTF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : kind == kSplitBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     CUresult r = g_encode(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(g_last_error, sizeof(g_last_error), "cuTensorMapEncodeTiled (16-bit) failed (%d)", (int)r);
         return FMM_ERR_CUDA;
@@ -536,10 +539,10 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
             const size_t off = (size_t)k0 * p->es16();   // bytes; k0 is a multiple of 8
             for (int i = 0; i < 2; ++i) {
                 if ((s = encode_map16(&args.maps[i], static_cast<char*>(p->a16[i]) + off, bf, kc, p->M, 1, ld,
-                                      p->M * ld, kBM)) != FMM_OK)
+                                      p->M * ld, kBM, p->pair)) != FMM_OK)
                     return s;
                 if ((s = encode_map16(&args.maps[2 + i], static_cast<char*>(p->b16[i]) + off, bf, kc, p->N, 1, ld,
-                                      p->N * ld, p->pair ? 128 : p->bn)) != FMM_OK)
+                                      p->N * ld, p->pair ? 128 : p->bn, p->pair)) != FMM_OK)
                     return s;
             }
             G.map_a = 0; G.map_a_lo = 1; G.map_b = 2; G.map_b_lo = 3;
@@ -723,8 +726,10 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
         const long long batch = Lf.nodes, ld = p->ld16;
         const int bf = p->split_kind;
         for (int i = 0; i < 2; ++i) {
-            if ((s = encode_map16(&maps[nm + i], p->a16[i], bf, kk, mm, batch, ld, mm * ld, kBM)) != FMM_OK) return s;
-            if ((s = encode_map16(&maps[nm + 2 + i], p->b16[i], bf, kk, nn, batch, ld, nn * ld, p->pair ? 128 : p->bn)) !=
+            if ((s = encode_map16(&maps[nm + i], p->a16[i], bf, kk, mm, batch, ld, mm * ld, kBM, p->pair)) != FMM_OK)
+                return s;
+            if ((s = encode_map16(&maps[nm + 2 + i], p->b16[i], bf, kk, nn, batch, ld, nn * ld, p->pair ? 128 : p->bn,
+                                  p->pair)) !=
                 FMM_OK)
                 return s;
         }

@@ -482,12 +482,13 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
 //              CTA's producer waits on its own empty barrier
 template <int MODE>
 struct PairCfg {
-    static constexpr bool kPlain = MODE == kLeafTF32;          // fp32 A | B tiles, 128-byte rows, one product
+    static constexpr bool kPlain = MODE == kLeafTF32;          // fp32 A | B tiles, one product
     static constexpr int kRows = 128;                          // rows per CTA of A and of B^T
-    // split planes: A hi | B hi | A lo | B lo with 64-byte rows; TF32: A | B with 128-byte rows
-    static constexpr int kStageBytes = 4 * kRows * 64;
-    static constexpr int kStages = 6;
-    static constexpr int kKB = MODE == kLeaf3xTF32P ? 16 : 32;   // K elements per stage (one row)
+    // 128-byte rows (128-byte swizzle): split planes A hi | B hi | A lo | B lo,
+    // 64 KB per stage; TF32: A | B, 32 KB per stage
+    static constexpr int kStageBytes = (kPlain ? 2 : 4) * kRows * 128;
+    static constexpr int kStages = kPlain ? 6 : 3;
+    static constexpr int kKB = (MODE == kLeaf3xTF32P || kPlain) ? 32 : 64;   // K elements per stage (one row)
     static constexpr int kTmemCols = 512;                      // 2 x 256-column accumulators
     static constexpr int kBarBytes = 256;
     static constexpr int kThreads = 256;
@@ -589,7 +590,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                         tma_load_3d_pair(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
                         tma_load_3d_pair(ah + Cfg::kRows * 128, maps + G.map_b, full_bar(stage), x, b0, bb);
                     } else {
-                        const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+                        const uint32_t bh = ah + Cfg::kRows * 128, al = bh + Cfg::kRows * 128, bl = al + Cfg::kRows * 128;
                         tma_load_3d_pair(ah, maps + G.map_a, full_bar(stage), x, a0, ab);
                         tma_load_3d_pair(bh, maps + G.map_b, full_bar(stage), x, b0, bb);
                         tma_load_3d_pair(al, maps + G.map_a_lo, full_bar(stage), x, a0, ab);
@@ -638,14 +639,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                             mma_tf32_pair(d, sdesc_kmajor_sw128(ah + kk * 32), sdesc_kmajor_sw128(bh + kk * 32), idesc,
                                           (kb == 0 && kk == 0) ? 0u : 1u);
                     } else {
-                        const uint32_t bh = ah + Cfg::kRows * 64, al = bh + Cfg::kRows * 64, bl = al + Cfg::kRows * 64;
+                        // hi / lo tiles with 128-byte rows: 4 MMAs of 32 bytes of K per product
+                        const uint32_t bh = ah + Cfg::kRows * 128, al = bh + Cfg::kRows * 128, bl = al + Cfg::kRows * 128;
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
+                        for (int kk = 0; kk < 4; ++kk) {
                             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-                            const uint64_t ahd = sdesc_kmajor_sw64(ah + kk * 32);
-                            const uint64_t bhd = sdesc_kmajor_sw64(bh + kk * 32);
-                            const uint64_t ald = sdesc_kmajor_sw64(al + kk * 32);
-                            const uint64_t bld = sdesc_kmajor_sw64(bl + kk * 32);
+                            const uint64_t ahd = sdesc_kmajor_sw128(ah + kk * 32);
+                            const uint64_t bhd = sdesc_kmajor_sw128(bh + kk * 32);
+                            const uint64_t ald = sdesc_kmajor_sw128(al + kk * 32);
+                            const uint64_t bld = sdesc_kmajor_sw128(bl + kk * 32);
                             if constexpr (MODE == kLeaf3xTF32P) {
                                 mma_tf32_pair(d, ald, bhd, idesc, first);  // lo_a * hi_b
                                 mma_tf32_pair(d, ahd, bld, idesc, 1u);     // hi_a * lo_b
