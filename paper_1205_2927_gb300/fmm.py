@@ -82,6 +82,10 @@ def _load():
     lib.fmm_plan_phase_bytes.restype = C.c_int
     lib.fmm_wait_selftest.argtypes = [vp, i64, vp]
     lib.fmm_wait_selftest.restype = C.c_int
+    lib.fmm_residual.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, vp, sz, C.POINTER(sz), C.c_int, vp]
+    lib.fmm_residual.restype = C.c_int
+    lib.fmm_gemm_static.argtypes = [i64, i64, i64, C.c_float, vp, i64, vp, i64, C.c_float, vp, i64, vp]
+    lib.fmm_gemm_static.restype = C.c_int
     return lib
 
 
@@ -160,6 +164,35 @@ def fmm_plan_profile_read(plan):
     v = [C.c_double() for _ in range(3)] + [C.c_int64(), C.c_int64()]
     _check(_lib.fmm_plan_profile_read(plan, *[C.byref(x) for x in v]), "fmm_plan_profile_read")
     return dict(pre_ms=v[0].value, leaf_ms=v[1].value, post_ms=v[2].value, launches=v[3].value, calls=v[4].value)
+
+
+def fmm_residual(A, B, Cm, x, fp64=False, stream=None):
+    """Freivalds residual r = Cm x - A (B x) of device tensors (row-major, unit
+    column stride; x: N float32 entries); returns r (M float64 entries, device)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    need = C.c_size_t(0)
+    _check(_lib.fmm_residual(M, N, K, None, max(A.stride(0), 1), None, max(B.stride(0), 1), None,
+                             max(Cm.stride(0), 1), None, None, None, 0, C.byref(need), int(fp64), None),
+           "fmm_residual(query)")
+    ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=A.device)
+    r = torch.empty(M, dtype=torch.float64, device=A.device)
+    _check(_lib.fmm_residual(M, N, K, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
+                             Cm.data_ptr(), max(Cm.stride(0), 1), x.data_ptr(), r.data_ptr(), ws.data_ptr(),
+                             ws.numel(), C.byref(need), int(fp64), _stream_ptr(stream)), "fmm_residual")
+    return r
+
+
+def fmm_gemm_static(A, B, Cm, alpha=1.0, beta=0.0, stream=None):
+    """Cm <- alpha A B + beta Cm through the allocation-free entry point (device
+    tensors, row-major, unit column stride; M, N, K <= 1024)."""
+    M, K = A.shape
+    N = B.shape[1]
+    _check(_lib.fmm_gemm_static(M, N, K, float(alpha), A.data_ptr(), max(A.stride(0), 1), B.data_ptr(),
+                                max(B.stride(0), 1), float(beta), Cm.data_ptr(), max(Cm.stride(0), 1),
+                                _stream_ptr(stream)), "fmm_gemm_static")
+    return Cm
 
 
 def fmm_plan_phase_bytes(plan):

@@ -196,7 +196,6 @@ def test_peel_blas_semantics(fmm):
 
 @pytest.mark.parametrize("fp64", [0, 1])
 def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64):
-    import ctypes
     import torch
     m, k, n = 700, 500, 600
     A = I.small_int((m, k), 21, r=3)
@@ -205,18 +204,7 @@ def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64):
     Cx[123, 45] += 1.0
     x = I.rademacher(n, 23)
     dA, dB, dC, dx = (torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in (A, B, Cx, x))
-    r = torch.empty(m, dtype=torch.float64, device="cuda")
-    need = ctypes.c_size_t(0)
-    lib = fmm.library()
-    lib.fmm_residual.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_void_p, ctypes.c_int64] * 3 + \
-        [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
-         ctypes.c_int, ctypes.c_void_p]
-    assert lib.fmm_residual(m, n, k, None, k, None, n, None, n, None, None, None, 0, ctypes.byref(need), 0, None) == 0
-    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
-    st = lib.fmm_residual(m, n, k, dA.data_ptr(), k, dB.data_ptr(), n, dC.data_ptr(), n, dx.data_ptr(),
-                          r.data_ptr(), ws.data_ptr(), need.value, None, fp64,
-                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert st == 0
+    r = fmm.fmm_residual(dA, dB, dC, dx, fp64=bool(fp64))
     torch.cuda.synchronize()
     got = r.cpu().numpy()
     want = O.freivalds(A, B, Cx, x)
