@@ -341,6 +341,64 @@ class BatchedPlan:
             pass
 
 
+# ------------------------------------------------------------------ remaining C-ABI names
+
+def fmm_options_default():
+    """The library's default options (depth -1, cut-off 2048, FP32, PAD, FIXED, Winograd)."""
+    o = Options()
+    _check(_lib.fmm_options_default(C.byref(o)), "fmm_options_default")
+    return o
+
+
+def fmm_status_string(status):
+    return _lib.fmm_status_string(int(status)).decode()
+
+
+def fmm_last_error():
+    return _lib.fmm_last_error().decode()
+
+
+def fmm_wait_selftest(plan, limit_ns=20_000_000, stream=None):
+    _check(_lib.fmm_wait_selftest(plan, int(limit_ns), _stream_ptr(stream)), "fmm_wait_selftest")
+
+
+def fmm_batched_plan(As, Bs, Cs, alpha=1.0, beta=0.0, stream=None, **opt_kwargs):
+    """Plan for the batched products C_i = alpha_i A_i B_i + beta_i C_i (a BatchedPlan)."""
+    return BatchedPlan(As, Bs, Cs, alpha=alpha, beta=beta, stream=stream, **opt_kwargs)
+
+
+def fmm_batched_run(bplan, stream=None):
+    bplan.run(stream)
+
+
+def fmm_batched_info(bplan):
+    return bplan.info()
+
+
+def fmm_batched_free(bplan):
+    bplan.close()
+
+
+def fmm_gemm_batched(As, Bs, Cs, alpha=1.0, beta=0.0, stream=None, **opt_kwargs):
+    """One-shot batched call (plan, run on `stream`, release the host state)."""
+    import torch
+    n = len(As)
+    i64, vp, f = C.c_int64 * n, C.c_void_p * n, C.c_float * n
+    al = [alpha] * n if not isinstance(alpha, (list, tuple)) else alpha
+    be = [beta] * n if not isinstance(beta, (list, tuple)) else beta
+    arrs = (i64(*[a.shape[0] for a in As]), i64(*[b.shape[1] for b in Bs]), i64(*[a.shape[1] for a in As]),
+            vp(*[a.data_ptr() for a in As]), i64(*[max(a.stride(0), 1) for a in As]),
+            vp(*[b.data_ptr() for b in Bs]), i64(*[max(b.stride(0), 1) for b in Bs]),
+            vp(*[c.data_ptr() for c in Cs]), i64(*[max(c.stride(0), 1) for c in Cs]), f(*al), f(*be))
+    opt = options(**opt_kwargs)
+    need = C.c_size_t(0)
+    _check(_lib.fmm_gemm_batched(n, *arrs, C.byref(opt), None, 0, C.byref(need), None), "fmm_gemm_batched(query)")
+    ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=As[0].device if n else "cuda")
+    _check(_lib.fmm_gemm_batched(n, *arrs, C.byref(opt), C.c_void_p(ws.data_ptr()), ws.numel(), C.byref(need),
+                                 _stream_ptr(stream)), "fmm_gemm_batched")
+    return ws   # the device tables live in the workspace until the launch has run
+
+
 # ------------------------------------------------------------------ planner / cost model
 
 NPARAM = 4673

@@ -38,6 +38,15 @@ def test_every_declared_symbol_is_exported(F):
     assert not missing, missing
 
 
+def test_every_declared_symbol_has_a_binding(F):
+    # the binding carries the C-ABI's names (argument marshalling only)
+    missing = [n for n in declared_functions() if not callable(getattr(F, n, None))]
+    assert not missing, missing
+    o = F.fmm_options_default()
+    assert (o.depth, o.cutoff) == (-1, 2048)
+    assert F.fmm_status_string(7) == "FMM_ERR_TIMEOUT"
+
+
 def test_options_default(F):
     o = F.options()
     assert (o.depth, o.cutoff, o.leaf_tile, o.precision, o.odd, o.planner, o.algo) == (-1, 2048, 0, 0, 0, 0, 0)

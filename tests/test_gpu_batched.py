@@ -97,3 +97,21 @@ def test_batched_graph_capture_replay(F):
     for (A, B), Cd in zip(probs, Cs):
         ref = O.classical(-A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
         assert np.array_equal(Cd.cpu().numpy(), ref)
+
+
+def test_one_shot_gemm_batched_and_unsupported_forms(F):
+    # fmm_gemm_batched: plan + run + release in one call, through the binding
+    import torch
+    probs = _problems(20, 9500, lo=16, hi=600, mult=1)
+    As, Bs, Cs = _upload(probs)
+    ws = F.fmm_gemm_batched(As, Bs, Cs, cutoff=128)
+    torch.cuda.synchronize()
+    del ws
+    for (A, B), Cd in zip(probs, Cs):
+        ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+        assert np.array_equal(Cd.cpu().numpy(), ref)
+    # forms the batched path rejects before any device work
+    for kw in ({"precision": "fp16x3"}, {"odd": "peel"}, {"algo": "classical"}):
+        with pytest.raises(F.FmmError) as e:
+            F.fmm_gemm_batched(As, Bs, Cs, **kw)
+        assert e.value.status == 6
