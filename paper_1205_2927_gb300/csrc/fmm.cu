@@ -1676,6 +1676,9 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
         p->child->ws_bytes = p->child_ws_bytes;
         p->child->num_sms = di.num_sms;
         e = cudaMemsetAsync(p->child->status, 0, 64 * sizeof(unsigned), (cudaStream_t)stream);
+        // the child's kernels report into the host plan's status word, which
+        // fmm_get_device_status reads
+        p->child->status = p->status;
         // zero the quadrant buffers once: each call rewrites only the valid parts,
         // so the padding rows/columns stay zero
         const size_t qa = (size_t)(p->hm * p->hk), qb = (size_t)(p->hk * p->hn), qc = (size_t)(p->hm * p->hn);

@@ -98,3 +98,35 @@ def test_host_resident_equals_device_resident(F, d):
     assert p.device_status() == 0
     p.close()
     assert np.array_equal(host, dC.cpu().numpy())
+
+
+@pytest.mark.parametrize("m,k,n,d", [(1000, 700, 900, 3), (700, 1030, 610, 2), (1100, 900, 1300, 4)])
+def test_host_resident_ragged_sub_level_alpha_beta(F, m, k, n, d):
+    # depth >= 2: the first and last root products stream sub-quadrants (A11 and
+    # B11 in, C12 out); ragged sizes clip those sub-quadrant copies
+    r = 1 if d == 4 else 2   # every partial sum stays an integer below 2^24
+    A = I.small_int((m, k), 16000 + m, r=r)
+    B = I.small_int((k, n), 16100 + n, r=r)
+    C0 = I.small_int((m, n), 16200 + d, r=4)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
+    C = run_host(F, A, B, C0, alpha=-1.0, beta=3.0, depth=d)
+    assert np.array_equal(C, (-ref + 3.0 * C0).astype(np.float32))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_host_resident_ragged_equals_device_resident(F, d):
+    # float data on ragged rectangular sizes: the padded device plan and the
+    # streamed plan (sub-level first and last products) agree bit for bit
+    import torch
+    m, k, n = 1000, 1100, 900
+    A, B = I.operands(m, k, n, I.seed_for(2, 60 + d), "normal")
+    C0 = I.uniform((m, n), 61 + d)
+    host = run_host(F, A, B, C0, alpha=1.5, beta=0.25, depth=d)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.from_numpy(C0).cuda()
+    p = F.Plan(m, n, k, depth=d)
+    p(dA, dB, dC, alpha=1.5, beta=0.25)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    p.close()
+    assert np.array_equal(host, dC.cpu().numpy())
