@@ -867,8 +867,36 @@ __global__ void __launch_bounds__(128) post_add2_kernel(const float* __restrict_
 // every product loaded once.  Level-2 outputs (the U-chain over l), then each
 // level-1 child's 16 values (the U-chain over j), then the node's 64 values
 // (the U-chain over i): the fp32 operations of three post_add passes.
+//
+// The level-1 children are visited in the order P1, P6, P7, P5, P3, P4, P2, in
+// which the node's U-chain needs them; the chain keeps three running values per
+// position (P1, U2 then U4, U3) and each node quadrant is stored as soon as it
+// is final (C22 = U7 after P5, C12 = U5 after P3, C21 = U6 after P4, C11 = U1
+// after P2).  48 live values instead of the seven children's 112 leave room
+// for four blocks per SM, i.e. twice the loads in flight.
+
+// Level-1 child I's 16 values at (quadrant q1, sub-quadrant q2): o1[q1 * 4 + q2].
+template <int I>
+__device__ __forceinline__ void post3_child(const float* __restrict__ pr, long long cs, float (&o1)[16]) {
+    float o2[7][4];   // level-2 child (I, j), quadrant q2
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        float p[7];
+#pragma unroll
+        for (int l = 0; l < 7; ++l) p[l] = __ldg(pr + ((I * 7 + j) * 7 + l) * cs);
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) o2[j][q2] = uchain_quadrant(q2, p[0], p[1], p[2], p[3], p[4], p[5], p[6]);
+    }
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2)
+            o1[q1 * 4 + q2] = uchain_quadrant(q1, o2[0][q2], o2[1][q2], o2[2][q2], o2[3][q2], o2[4][q2], o2[5][q2],
+                                              o2[6][q2]);
+}
+
 template <bool ROOT>
-__global__ void __launch_bounds__(128, 2) post_add3_kernel(const float* __restrict__ P, long long ld_in, long long cs,
+__global__ void __launch_bounds__(128, 4) post_add3_kernel(const float* __restrict__ P, long long ld_in, long long cs,
                                                         long long h, long long w, float* out, long long ld_out,
                                                         long long out_ns, long long valid_rows, long long valid_cols,
                                                         float alpha, float beta) {
@@ -879,41 +907,43 @@ __global__ void __launch_bounds__(128, 2) post_add3_kernel(const float* __restri
     float* o = out + node * out_ns;
     for (long long r = blockIdx.y; r < h; r += gridDim.y) {
         const float* pr = base + r * ld_in + c;
-        float o1[7][16];   // level-1 child i at (quadrant q1, sub-quadrant q2): [q1 * 4 + q2]
-#pragma unroll
-        for (int i = 0; i < 7; ++i) {
-            float o2[7][4];   // level-2 child (i, j), quadrant q2
-#pragma unroll
-            for (int j = 0; j < 7; ++j) {
-                float p[7];
-#pragma unroll
-                for (int l = 0; l < 7; ++l) p[l] = __ldg(pr + ((i * 7 + j) * 7 + l) * cs);
-#pragma unroll
-                for (int q2 = 0; q2 < 4; ++q2) o2[j][q2] = uchain_quadrant(q2, p[0], p[1], p[2], p[3], p[4], p[5], p[6]);
-            }
-#pragma unroll
-            for (int q1 = 0; q1 < 4; ++q1)
-#pragma unroll
-                for (int q2 = 0; q2 < 4; ++q2)
-                    o1[i][q1 * 4 + q2] = uchain_quadrant(q1, o2[0][q2], o2[1][q2], o2[2][q2], o2[3][q2], o2[4][q2],
-                                                         o2[5][q2], o2[6][q2]);
-        }
-#pragma unroll
-        for (int s = 0; s < 16; ++s) {            // (q1, q2)
+        // node quadrant q0 at position s = (q1, q2)
+        auto put = [&](int q0, int s, float v) {
             const int q1 = s >> 2, q2 = s & 3;
-#pragma unroll
-            for (int q0 = 0; q0 < 4; ++q0) {
-                const long long rr = (long long)(4 * (q0 >> 1) + 2 * (q1 >> 1) + (q2 >> 1)) * h + r;
-                const long long cc = (long long)(4 * (q0 & 1) + 2 * (q1 & 1) + (q2 & 1)) * w + c;
-                const float v = uchain_quadrant(q0, o1[0][s], o1[1][s], o1[2][s], o1[3][s], o1[4][s], o1[5][s], o1[6][s]);
-                if (!ROOT) {
-                    o[rr * ld_out + cc] = v;
-                } else if (rr < valid_rows && cc < valid_cols) {
-                    float* dst = o + rr * ld_out + cc;
-                    *dst = (beta != 0.0f) ? alpha * v + beta * *dst : alpha * v;
-                }
+            const long long rr = (long long)(4 * (q0 >> 1) + 2 * (q1 >> 1) + (q2 >> 1)) * h + r;
+            const long long cc = (long long)(4 * (q0 & 1) + 2 * (q1 & 1) + (q2 & 1)) * w + c;
+            if (!ROOT) {
+                o[rr * ld_out + cc] = v;
+            } else if (rr < valid_rows && cc < valid_cols) {
+                float* dst = o + rr * ld_out + cc;
+                *dst = (beta != 0.0f) ? alpha * v + beta * *dst : alpha * v;
             }
+        };
+        float o1[16], a1[16], u2[16], u3[16];
+        post3_child<0>(pr, cs, o1);                                  // P1
+#pragma unroll
+        for (int s = 0; s < 16; ++s) a1[s] = o1[s];
+        post3_child<5>(pr, cs, o1);                                  // P6: U2 = P1 + P6
+#pragma unroll
+        for (int s = 0; s < 16; ++s) u2[s] = a1[s] + o1[s];
+        post3_child<6>(pr, cs, o1);                                  // P7: U3 = U2 + P7
+#pragma unroll
+        for (int s = 0; s < 16; ++s) u3[s] = u2[s] + o1[s];
+        post3_child<4>(pr, cs, o1);                                  // P5: U4 = U2 + P5, C22 = U7 = U3 + P5
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            u2[s] = u2[s] + o1[s];
+            put(3, s, u3[s] + o1[s]);
         }
+        post3_child<2>(pr, cs, o1);                                  // P3: C12 = U5 = U4 + P3
+#pragma unroll
+        for (int s = 0; s < 16; ++s) put(1, s, u2[s] + o1[s]);
+        post3_child<3>(pr, cs, o1);                                  // P4: C21 = U6 = U3 - P4
+#pragma unroll
+        for (int s = 0; s < 16; ++s) put(2, s, u3[s] - o1[s]);
+        post3_child<1>(pr, cs, o1);                                  // P2: C11 = U1 = P1 + P2
+#pragma unroll
+        for (int s = 0; s < 16; ++s) put(0, s, a1[s] + o1[s]);
     }
 }
 
