@@ -351,7 +351,9 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                                 const float4 o = *reinterpret_cast<const float4*>(cp + j);
                                 v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
                             }
-                            *reinterpret_cast<float4*>(cp + j) = v;
+                            // evict-first: the products are read only after the
+                            // whole launch, and must not push operand lines out of L2
+                            __stcs(reinterpret_cast<float4*>(cp + j), v);
                         }
                     } else {
                         const int lim = min(32, G.N - col0);
@@ -712,7 +714,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                                 const float4 o = *reinterpret_cast<const float4*>(cp + j);
                                 v.x += beta * o.x; v.y += beta * o.y; v.z += beta * o.z; v.w += beta * o.w;
                             }
-                            *reinterpret_cast<float4*>(cp + j) = v;
+                            // evict-first: the products are read only after the
+                            // whole launch, and must not push operand lines out of L2
+                            __stcs(reinterpret_cast<float4*>(cp + j), v);
                         }
                     } else {
                         const int lim = min(32, G.N - col0);
