@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--leaf-tile", type=int, default=0)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-classical", action="store_true")
+    ap.add_argument("--no-split", action="store_true",
+                    help="skip the split-precision (FP16x3, BF16x3) runs reported beside plain FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="square",
@@ -588,6 +590,29 @@ def main():
         classical = {"gflops": round(flops * world / cms / 1e6, 1), "ms_per_step": round(cms, 3)}
         cplan.close()
 
+    # the split-precision forms beside plain FP32: same operands, same depth,
+    # each with its own classical (depth-0) GEMM and its error on the same
+    # float64 rows; outside the timed region of `value`
+    split = None
+    if args.precision == "fp32" and not args.no_split:
+        split = {"depth": depth, "bound": 2e-6}
+        dC2 = torch.empty((n, n), device="cuda")
+        for prec in ("fp16x3", "bf16x3"):
+            sp = fmm.Plan(n, n, n, depth=depth, precision=prec, leaf_tile=args.leaf_tile)
+            sms = timed(torch, dist, world, lambda: sp(dA, dB, dC2), min(args.steps, 10), 3)
+            assert sp.device_status() == 0, "device status word set"
+            sp.close()
+            entry = {"gflops": round(flops * world / sms / 1e6, 1), "ms_per_step": round(sms, 3),
+                     "error": sampled_error(np, torch, dC2, A_h, B_h)}
+            if classical:
+                sc = fmm.Plan(n, n, n, depth=0, precision=prec, leaf_tile=args.leaf_tile)
+                scms = timed(torch, dist, world, lambda: sc(dA, dB, dC2), min(args.steps, 10), 3)
+                sc.close()
+                entry["classical_gflops"] = round(flops * world / scms / 1e6, 1)
+                entry["speedup_vs_classical"] = round(scms / sms, 3)
+            split[prec] = entry
+        del dC2
+
     e2e = None
     if not args.no_e2e:
         # host-resident operands through the C ABI (host_operands = 1): the call
@@ -670,6 +695,7 @@ def main():
         "error": {"metric": "max|C-C64|/(max|A| max|B| n) on 16 sampled rows", "value": err, "bound": 2e-6},
         "classical": classical,
         "speedup_vs_classical": round(value / classical["gflops"], 3) if classical else None,
+        "split_precision": split,
         "phases": phases,
         "additions": additions,
         "roofline": roofline,
