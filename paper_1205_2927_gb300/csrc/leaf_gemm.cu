@@ -226,8 +226,9 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = make_idesc(2u, kBM, BN);
-            constexpr uint32_t idesc16 = make_idesc((MODE == kLeafBF16x3 || MODE == kLeafBF16x3P) ? 1u : 0u, kBM, BN);
+            constexpr uint32_t idesc_full = make_idesc(2u, kBM, BN);
+            constexpr uint32_t idesc16_full = make_idesc((MODE == kLeafBF16x3 || MODE == kLeafBF16x3P) ? 1u : 0u, kBM, BN);
+            static_assert(idesc_with_n(idesc_full, BN) == idesc_full, "N field of the instruction descriptor");
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -240,6 +241,12 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
+                // under the dynamic tile order the last tile column runs narrower
+                // MMAs; under static round robin a cheaper tile lets its CTA drift
+                // off its neighbours' operand panels, which costs more than it saves
+                const uint32_t ncols = dyn ? tile_cols(groups[g].N, tn, BN) : (uint32_t)BN;
+                const uint32_t idesc = idesc_with_n(idesc_full, ncols);
+                const uint32_t idesc16 = idesc_with_n(idesc16_full, ncols);
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
@@ -576,7 +583,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const GemmGroup& G = groups[g];
                 const int nk = (G.K + Cfg::kKB - 1) / Cfg::kKB;
-                const int a0 = tm * 256 + (int)rank * Cfg::kRows, b0 = tn * 256 + (int)rank * Cfg::kRows;
+                // the pair's MMA reads B rows [0, ncols / 2) of the tile from CTA 0
+                // and [ncols / 2, ncols) from CTA 1 (ncols < 256 in the last tile
+                // column under the dynamic tile order, as in the MMA issuer)
+                const int ncols = dyn ? (int)tile_cols(G.N, tn, 256) : 256;
+                const int a0 = tm * 256 + (int)rank * Cfg::kRows, b0 = tn * 256 + (int)rank * (ncols / 2);
                 const int ab = b + G.a_batch_off, bb = b + G.b_batch_off;
                 for (int kb = 0; kb < nk; ++kb) {
                     // the stage is free in this CTA once the MMAs that read it
@@ -610,7 +621,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         // ------------------------------------------------ MMA issuer (CTA 0)
         if (lane == 0 && rank == 0) {
             constexpr uint32_t fmt = (MODE == kLeaf3xTF32P || MODE == kLeafTF32) ? 2u : (MODE == kLeafBF16x3P ? 1u : 0u);
-            constexpr uint32_t idesc = make_idesc(fmt, 256, 256);
+            constexpr uint32_t idesc_full = make_idesc(fmt, 256, 256);
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -623,6 +634,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 int g, b, tm, tn;
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
+                const uint32_t idesc = idesc_with_n(idesc_full, dyn ? tile_cols(groups[g].N, tn, 256) : 256u);
                 if (!mbar_wait_cluster(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 256);

@@ -280,6 +280,19 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, int M, int
            | (static_cast<uint32_t>(M >> 4) << 24); // M / 16
 }
 
+// Width of a tile's MMAs: the full tile width, or for the last tile column of
+// an operand the valid columns rounded up to a multiple of 32 (a valid N for
+// M = 128 on one CTA and M = 256 on a CTA pair).  Columns past the valid ones
+// are never stored, so narrowing the MMA only drops work on zero-filled rows.
+__host__ __device__ constexpr uint32_t tile_cols(int n_total, int tn, int width) {
+    return n_total - tn * width >= width ? (uint32_t)width : (uint32_t)((n_total - tn * width + 31) & ~31);
+}
+
+// The instruction descriptor with its N field set to n (a multiple of 16, 16..256).
+__host__ __device__ constexpr uint32_t idesc_with_n(uint32_t idesc, uint32_t n) {
+    return (idesc & ~(0x3Fu << 17)) | ((n >> 3) << 17);
+}
+
 // 32 lanes x 32 columns of 32-bit TMEM cells -> 32 registers per thread
 // (thread t of the warp gets lane base+t, columns col..col+31).
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {

@@ -302,6 +302,22 @@ def test_pair_leaves_bit_exact(fmm, prec, m, k, n, d):
     assert np.array_equal(C, ref)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32"])
+@pytest.mark.parametrize("tile", [512, 256, 128])
+@pytest.mark.parametrize("n", [560, 912, 1030])
+def test_narrow_last_tile_column_bit_exact(fmm, prec, tile, n):
+    # depth 1 with leaves of K = 1024 runs the dynamic tile order, under which
+    # the last tile column of each leaf issues MMAs of the valid width rounded
+    # up to 32 (leaf widths 280, 456, 516: remainders 24, 200 / 72 and 4)
+    m, k = 600, 2048
+    A = I.small_int((m, k), 17000 + n + tile, r=1)
+    B = I.small_int((k, n), 17100 + n + tile, r=1)
+    C, info = run(fmm, A, B, depth=1, precision=prec, leaf_tile=tile)
+    assert (info["depth"], info["leaf_tile"]) == (1, tile)
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    assert np.array_equal(C, ref)
+
+
 def test_pair_leaves_float_and_blas(fmm):
     n = 1024
     A, B = I.operands(n, n, n, I.seed_for(1, 21), "normal")
