@@ -6,6 +6,7 @@ step and checks that a pin catches it."""
 import fractions
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -81,6 +82,18 @@ def test_quadrant_shapes_eq1(m, n):
     top = np.concatenate([D0, D1], axis=1)
     bot = np.concatenate([D2, D3], axis=1)
     assert np.array_equal(np.concatenate([top, bot], axis=0), D)
+
+
+def test_odd_border_counts_golden():
+    # tests/golden/eq1_odd_border_counts.txt: the quadrant shapes of Eq. 1 and
+    # the paper's count of C0's border elements (2N - 1) for odd n = 2N - 1
+    path = os.path.join(os.path.dirname(__file__), "golden", "eq1_odd_border_counts.txt")
+    rows = [list(map(int, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) >= 5
+    for n, r0, c0, r3, c3, extra in rows:
+        D0, _, _, D3 = O.quadrants(np.zeros((n, n)))
+        assert D0.shape == (r0, c0) and D3.shape == (r3, c3)
+        assert D0.size - D3.size == extra == n
 
 
 # --- Table 1 -------------------------------------------------------------------
