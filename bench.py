@@ -396,7 +396,7 @@ def wl_batched(args):
     Cs = [torch.empty((m, n), device="cuda") for m, k, n in shapes]
     best = None
     t_tune0 = time.perf_counter()
-    for bn in (128, 256):
+    for bn in (128, 256, 512):
         for cutoff in (1024, 2048, 8192):
             bp = fmm.BatchedPlan(As, Bs, Cs, leaf_tile=bn, cutoff=cutoff)
             s = torch.cuda.Stream()

@@ -92,8 +92,9 @@ typedef struct {
     int depth;                 /* recursion levels; -1 = chosen by the planner */
     int cutoff;                /* planner: smallest leaf dimension worth a level (elements) */
     int leaf_tile;             /* leaf tile: 128 or 256 (128 x N tile on one SM), 512 (256 x 256
-                                  tile on a pair of SMs; batched plans and a peeled border use
-                                  256 instead); 0 = chosen with the depth */
+                                  tile on a pair of SMs; TF32 batched plans and a peeled border
+                                  use 256 instead); 0 = chosen with the depth (batched: 512,
+                                  or 256 for TF32) */
     fmm_precision_t precision;
     fmm_odd_t odd;
     fmm_planner_t planner;

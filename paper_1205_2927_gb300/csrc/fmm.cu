@@ -888,6 +888,7 @@ fmm_status_t execute(fmm_plan_s* p, float alpha, const float* A, const float* B,
 struct fmm_batched_s {
     int count = 0;
     int bn = 256, mode = kLeaf3xTF32, num_sms = 0;
+    int pair = 0;                      // leaf tiles of 256 x 256 on CTA pairs (pre-split precisions)
     unsigned* status = nullptr;
     CUtensorMap* d_maps = nullptr;
     GemmGroup* d_groups = nullptr;
@@ -922,9 +923,13 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     Carver cv(ws);
     b->status = cv.take<unsigned>(64);
     b->count = count;
-    b->bn = (o.leaf_tile && o.leaf_tile != 512) ? o.leaf_tile : 256;   // batched launches stay single-CTA
     b->mode = leaf_mode(o.precision);
     b->pre = o.precision == FMM_PREC_FP32 || o.precision == FMM_PREC_BF16X3;
+    // leaf tile 512 (and the default 0): 256 x 256 tiles on CTA pairs for the
+    // pre-split precisions (512 uneven products: 8.70 ms per replay against 9.10
+    // on single CTAs); TF32 batched launches stay on single CTAs (128 x 256)
+    b->pair = ((o.leaf_tile == 512 || o.leaf_tile == 0) && b->pre) ? 1 : 0;
+    b->bn = (o.leaf_tile && o.leaf_tile != 512) ? o.leaf_tile : 256;
     if (b->pre) {
         b->split_kind = o.precision == FMM_PREC_BF16X3 ? kSplitBF16 : kSplitTF32;
         b->mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : kLeaf3xTF32P;
@@ -968,10 +973,12 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 127) / 128), 1});
             fmm_status_t s;
             const int kd = b->split_kind;
-            if ((s = encode_map16(&maps[nm], ah, kd, K[i], M[i], 1, ld, M[i] * ld, kBM)) != FMM_OK) return s;
-            if ((s = encode_map16(&maps[nm + 1], al, kd, K[i], M[i], 1, ld, M[i] * ld, kBM)) != FMM_OK) return s;
-            if ((s = encode_map16(&maps[nm + 2], bh, kd, K[i], N[i], 1, ld, N[i] * ld, b->bn)) != FMM_OK) return s;
-            if ((s = encode_map16(&maps[nm + 3], bl, kd, K[i], N[i], 1, ld, N[i] * ld, b->bn)) != FMM_OK) return s;
+            const bool wide = b->pair != 0;              // pair: 128-byte rows, 128 rows of B per CTA
+            const int bbox = wide ? 128 : b->bn;
+            if ((s = encode_map16(&maps[nm], ah, kd, K[i], M[i], 1, ld, M[i] * ld, kBM, wide)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 1], al, kd, K[i], M[i], 1, ld, M[i] * ld, kBM, wide)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 2], bh, kd, K[i], N[i], 1, ld, N[i] * ld, bbox, wide)) != FMM_OK) return s;
+            if ((s = encode_map16(&maps[nm + 3], bl, kd, K[i], N[i], 1, ld, N[i] * ld, bbox, wide)) != FMM_OK) return s;
             GemmGroup& G = groups[ng++];
             memset(&G, 0, sizeof(G));
             G.M = (int)M[i]; G.N = (int)N[i]; G.K = (int)K[i]; G.batch = 1;
@@ -1009,6 +1016,7 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             tmp.opt = o;
             tmp.depth = d;
             tmp.bn = b->bn;
+            tmp.pair = b->pair;
             tmp.mode = b->mode;
             tmp.peel = 0;
             tmp.pre16 = b->pre;
@@ -1036,7 +1044,8 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     long long t = 0;
     for (int g = 0; g < ng; ++g) {
         GemmGroup& G = groups[g];
-        G.tiles_m = (G.M + kBM - 1) / kBM;
+        const int tile_rows = b->pair ? 256 : kBM;
+        G.tiles_m = (G.M + tile_rows - 1) / tile_rows;
         G.tiles_n = (G.N + b->bn - 1) / b->bn;
         G.tile_begin = t;
         t += (long long)G.tiles_m * G.tiles_n * G.batch;
@@ -1572,7 +1581,8 @@ fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
         args.status = b->status;
         // static round robin over tiles sorted by K (longest first) balances the
         // uneven tiles like LPT; dynamic order measured 2.5 % slower here
-        FMM_CUDA(launch_leaf_gemm(args, b->mode, b->bn, b->num_sms, stream));
+        if (b->pair) FMM_CUDA(launch_leaf_gemm_pair(args, b->mode, b->num_sms, stream));
+        else FMM_CUDA(launch_leaf_gemm(args, b->mode, b->bn, b->num_sms, stream));
         b->launches += 1;
     }
     for (size_t j = 0; j < b->subs.size(); ++j) {

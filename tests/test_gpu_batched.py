@@ -34,7 +34,7 @@ def _upload(probs):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32"])
-@pytest.mark.parametrize("cutoff,bn", [(4096, 256), (64, 256), (64, 128)])
+@pytest.mark.parametrize("cutoff,bn", [(4096, 256), (64, 256), (64, 128), (4096, 512), (64, 512)])
 def test_batched_bit_exact_small_int(F, cutoff, bn, prec):
     import torch
     probs = _problems(48, 9100, lo=16, hi=700, mult=1)
@@ -51,7 +51,10 @@ def test_batched_bit_exact_small_int(F, cutoff, bn, prec):
     bp.close()
 
 
-def test_batched_alpha_beta_and_float_bound(F):
+@pytest.mark.parametrize("bn", [0, 512])
+def test_batched_alpha_beta_and_float_bound(F, bn):
+    # bn 512: leaf tiles of 256 x 256 on CTA pairs (the depth-0 problems and the
+    # leaves of the recursing ones in the same persistent launch)
     import torch
     shapes = I.batched_shapes(24, 9200, lo=64, hi=1024, multiple=4)
     probs = [I.operands(m, k, n, 9300 + i) for i, (m, k, n) in enumerate(shapes)]
@@ -59,7 +62,7 @@ def test_batched_alpha_beta_and_float_bound(F):
     Bs = [torch.from_numpy(B).cuda() for _, B in probs]
     C0 = [I.uniform((A.shape[0], B.shape[1]), 9400 + i) for i, (A, B) in enumerate(probs)]
     Cs = [torch.from_numpy(c).cuda() for c in C0]
-    bp = F.BatchedPlan(As, Bs, Cs, alpha=0.5, beta=2.0, cutoff=256)
+    bp = F.BatchedPlan(As, Bs, Cs, alpha=0.5, beta=2.0, cutoff=256, leaf_tile=bn)
     bp.run()
     torch.cuda.synchronize()
     for (A, B), c0, Cd in zip(probs, C0, Cs):

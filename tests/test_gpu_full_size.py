@@ -101,7 +101,8 @@ def test_rectangular_19000x12000x15000_split_precision(F, prec, dist, d, bound):
     check(A, B, C, sample_rows(m, d, 3), bound, I.seed_for(3, 92))
 
 
-def test_batched_512_uneven(F):
+@pytest.mark.parametrize("tile", [256, 512])
+def test_batched_512_uneven(F, tile):
     import torch
     shapes = I.batched_shapes(512, I.seed_for(4, 0))
     As = [I.uniform((m, k), I.seed_for(4, 1) + 3 * i) for i, (m, k, n) in enumerate(shapes)]
@@ -109,7 +110,7 @@ def test_batched_512_uneven(F):
     dA = [torch.from_numpy(a).cuda() for a in As]
     dB = [torch.from_numpy(b).cuda() for b in Bs]
     dC = [torch.empty((m, n), device="cuda") for m, k, n in shapes]
-    bp = F.BatchedPlan(dA, dB, dC, leaf_tile=256, cutoff=1024)
+    bp = F.BatchedPlan(dA, dB, dC, leaf_tile=tile, cutoff=1024)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
