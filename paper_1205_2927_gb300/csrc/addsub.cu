@@ -738,6 +738,88 @@ __global__ void __launch_bounds__(256, 2) pre_add3_kernel(View P, long long h, l
     }
 }
 
+// Root B side of a depth-3 plan in one pass, straight from the caller's
+// row-major B (valid K x N, zero outside) into the 343 leaf operands of B^T,
+// split into planes.  Leaf position (n, k) of B^T sub-block (a, b) is
+// B[b * w + k][a * h + n] (h = N0 / 8, w = K0 / 8).  A block takes an 8 (n) x
+// 32 (k) patch of positions: it stages the 64 sub-block tiles of B that the
+// patch needs (32 rows of k by 8 columns of n, one 32-byte sector per row) in
+// shared memory, every load issued before the first store; each thread then
+// reads its position's 64 values from there (rows padded to 9 floats, so the
+// 32 lanes of a warp -- 32 consecutive k -- hit 32 banks) and runs
+// pre_add3_kernel's chain, its leaf stores running along k, coalesced.  The
+// fp32 operations are those of pre_add3_kernel<1> on a transposed copy.
+constexpr int kBtN = 8, kBtK = 32, kBtPitch = 9;
+constexpr size_t kBtSmem = (size_t)64 * kBtK * kBtPitch * sizeof(float);   // 73,728 bytes
+
+template <int KIND>
+__global__ void __launch_bounds__(256, 2) pre_add3_bt_kernel(const float* __restrict__ B, long long ldb, long long K,
+                                                          long long N, long long h, long long w, long long tiles_n,
+                                                          Stack16 out, const float* __restrict__ scale) {
+    extern __shared__ float bt_tile[];   // [64 sub-blocks][kBtK rows of k][kBtPitch]
+    const float sc = scale ? scale[1] : 1.0f;
+    const int t = threadIdx.x;
+    const long long n0 = (long long)(blockIdx.x % tiles_n) * kBtN, k0 = (long long)(blockIdx.x / tiles_n) * kBtK;
+    const bool vec = (reinterpret_cast<uintptr_t>(B) & 15) == 0 && (ldb & 3) == 0;
+    // 64 tiles x 32 rows x 2 float4 = 4096 float4, 16 per thread
+    float4 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int L = t + 256 * j;   // sub-block L / 64 = 8 a + b, row (L % 64) / 2, half L % 2
+        const int ab = L >> 6, kr = (L & 63) >> 1, q = L & 1;
+        const long long k = k0 + kr, n = n0 + 4 * q;   // h is a multiple of 4: n < h covers n + 3
+        const long long row = (ab & 7) * w + k, col = (ab >> 3) * h + n;
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < w && n < h && row < K && col < N) {
+            const float* src = B + row * ldb + col;
+            if (vec && col + 3 < N) {
+                v[j] = __ldg(reinterpret_cast<const float4*>(src));
+            } else {
+                v[j].x = __ldg(src);
+                if (col + 1 < N) v[j].y = __ldg(src + 1);
+                if (col + 2 < N) v[j].z = __ldg(src + 2);
+                if (col + 3 < N) v[j].w = __ldg(src + 3);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int L = t + 256 * j;
+        float* d = bt_tile + ((L >> 6) * kBtK + ((L & 63) >> 1)) * kBtPitch + 4 * (L & 1);
+        d[0] = v[j].x; d[1] = v[j].y; d[2] = v[j].z; d[3] = v[j].w;
+    }
+    __syncthreads();
+    const int tn = t >> 5, tk = t & 31;
+    const long long n = n0 + tn, k = k0 + tk;
+    if (n >= h || k >= w) return;
+    float X[8][8];   // sub-block (a, b) of B^T at position (n, k)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) X[a][b] = bt_tile[((a * 8 + b) * kBtK + tk) * kBtPitch + tn];
+    const long long o0 = n * out.ld + k;
+#pragma unroll 1
+    for (int i = 0; i < 7; ++i) {
+        float Y[4][4];   // level-1 child i, sub-block (a, b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Y[a][b] = child_of1<1>(i, X[a][b], X[a][4 + b], X[4 + a][b], X[4 + a][4 + b]);
+#pragma unroll 1
+        for (int j = 0; j < 7; ++j) {
+            float Cj[4];   // level-2 child (i, j), quadrant t
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                Cj[q] = child_of1<1>(j, Y[(q >> 1)][(q & 1)], Y[(q >> 1)][2 + (q & 1)], Y[2 + (q >> 1)][(q & 1)],
+                                     Y[2 + (q >> 1)][2 + (q & 1)]);
+#pragma unroll
+            for (int l = 0; l < 7; ++l)
+                split_store1<KIND>(out.hi, out.lo, o0 + (i * 49 + j * 7 + l) * out.child_stride,
+                                   child_of1<1>(l, Cj[0], Cj[1], Cj[2], Cj[3]), sc);
+        }
+    }
+}
+
 // Root B side of a depth-2 plan in one pass, straight from the caller's
 // row-major B (valid K x N, zero outside) into the 49 leaf operands of B^T,
 // split into planes.  Leaf position (n, k) of B^T sub-block (a, b) is
@@ -1237,6 +1319,36 @@ cudaError_t launch_pre_add3(const View& node, long long nodes, const Stack16& ou
 #undef FMM_PRE3K
 #undef FMM_PRE3
     return cudaGetLastError();
+}
+
+template <int KIND>
+static cudaError_t launch_pre_add3_bt_impl(const float* B, long long ldb, long long K, long long N, long long h,
+                                           long long w, const Stack16& out, const float* scale,
+                                           cudaStream_t stream) {
+    // once per device and instantiation (keeps later launches free of other API calls)
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+        e = cudaFuncSetAttribute(pre_add3_bt_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBtSmem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_done[dev] = true;
+    }
+    const long long tiles_n = (h + kBtN - 1) / kBtN, tiles = tiles_n * ((w + kBtK - 1) / kBtK);
+    pre_add3_bt_kernel<KIND><<<(unsigned)tiles, 256, kBtSmem, stream>>>(B, ldb, K, N, h, w, tiles_n, out, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pre_add3_bt(const float* B, long long ldb, long long K, long long N, long long h, long long w,
+                               const Stack16& out, int kind, const float* scale, cudaStream_t stream) {
+    if (h <= 0 || w <= 0) return cudaSuccess;
+    if ((h & 3) != 0) return cudaErrorInvalidValue;   // float4 staging along n
+    switch (kind) {
+        case kSplitBF16: return launch_pre_add3_bt_impl<kSplitBF16>(B, ldb, K, N, h, w, out, scale, stream);
+        case kSplitFP16: return launch_pre_add3_bt_impl<kSplitFP16>(B, ldb, K, N, h, w, out, scale, stream);
+        default: return launch_pre_add3_bt_impl<kSplitTF32>(B, ldb, K, N, h, w, out, scale, stream);
+    }
 }
 
 cudaError_t launch_post_add3(const float* P, long long ld_in, long long child_stride, long long nodes, long long h,

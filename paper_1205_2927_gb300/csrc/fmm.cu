@@ -191,7 +191,6 @@ struct fmm_plan_s {
     // algorithmic bytes (reads + writes the passes need) of the last call's
     // addition phases: [0] before the leaf launch, [1] after it
     double acct[2] = {0.0, 0.0};
-    float* bt_root = nullptr;   // depth-3 split-plane plans: B^T zero-padded to N0 x K0
     // host-resident operands: root level depth-first over the 7 products with
     // quadrant transfers on two copy streams; children run on device buffers
     int host = 0;
@@ -314,10 +313,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             const long long per = L.full ? 7 : 4;
             if (p->fuse_pre() && (l == d - 3 || l == d - 2)) continue;   // written by no pass: fused away
             if (p->fuse_root_pre() && l == 0) continue;   // fused away (both sides read the caller's operands)
-            if (p->fuse_root_pre3() && l < d - 1) {   // fused away; B^T of the root instead
-                if (l == 0) p->bt_root = cv.take<float>((size_t)(p->N0 * p->K0));
-                continue;
-            }
+            if (p->fuse_root_pre3() && l < d - 1) continue;   // fused away (both sides read the caller's operands)
             if (p->pre16 && l == d - 1) {   // the leaves' operands, as split planes
                 p->ld16 = rup(C.k, 128 / (long long)p->es16());   // 128-byte row pitch
                 for (int i = 0; i < 2; ++i) p->a16[i] = cv.take<char>((size_t)(L.nodes * 7 * C.m * p->ld16) * p->es16());
@@ -635,13 +631,11 @@ fmm_status_t winograd_pre(fmm_plan_s* p, const float* A, const float* B, cudaStr
         Stack16 sa{p->a16[0], p->a16[1], p->ld16, Lf.m * p->ld16, 343};
         Stack16 sb{p->b16[0], p->b16[1], p->ld16, Lf.n * p->ld16, 343};
         FMM_CUDA(launch_pre_add3(va, 1, sa, 0, kind, scale, stream));
-        // B: one zero-padded transposed copy, then the same pass on B^T
-        FMM_CUDA(launch_transpose(B, p->ldb, p->Kw, p->Nw, p->bt_root, p->K0, stream, p->N0, p->K0));
-        View vb{p->bt_root, p->K0, 0, p->N0, p->K0, p->N0, p->K0};
-        FMM_CUDA(launch_pre_add3(vb, 1, sb, 1, kind, scale, stream));
-        p->launches += 3;
-        p->acct[0] += root_in + 4.0 * (double)(p->Kw * p->Nw + p->N0 * p->K0) +
-                      343.0 * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
+        // B: the caller's row-major B straight into the K-major leaf planes,
+        // transposed through shared memory
+        FMM_CUDA(launch_pre_add3_bt(B, p->ldb, p->Kw, p->Nw, Lf.n, Lf.k, sb, kind, scale, stream));
+        p->launches += 2;
+        p->acct[0] += root_in + 343.0 * (double)(Lf.m * Lf.k + Lf.n * Lf.k) * pl;
         return FMM_OK;
     }
     if (p->fuse_root_pre()) {

@@ -205,6 +205,10 @@ cudaError_t launch_pre_add2(const View& node, long long nodes, const Stack16& ou
 // into the 49 leaf operands of B^T (h = N0 / 4 rows, w = K0 / 4 columns each).
 cudaError_t launch_pre_add2_b_root(const float* B, long long ldb, long long K, long long N, long long h, long long w,
                                    const Stack16& out, int kind, const float* scale, cudaStream_t stream);
+// Root B side of a depth-3 plan straight from row-major B (valid K x N) into
+// the 343 leaf operands of B^T (h x w each, h a multiple of 4), split planes.
+cudaError_t launch_pre_add3_bt(const float* B, long long ldb, long long K, long long N, long long h, long long w,
+                               const Stack16& out, int kind, const float* scale, cudaStream_t stream);
 // Three levels at once (a depth-3 plan's whole recursion): node operands
 // (8h x 8w) -> 343 split leaf operands each; and 343 products per node -> the
 // node output (alpha / beta and the valid window at the root, valid_rows >= 0).
