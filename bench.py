@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--leaf-tile", type=int, default=0)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-classical", action="store_true")
+    ap.add_argument("--no-residual", action="store_true", help="skip timing the Freivalds residual check")
     ap.add_argument("--no-split", action="store_true",
                     help="skip the split-precision (FP16x3, BF16x3) runs reported beside plain FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -583,6 +584,22 @@ def main():
     # accuracy of the benchmarked result on sampled rows against a float64 product
     err = sampled_error(np, torch, dC, A_h, B_h)
 
+    # the residual check on the benchmarked product: r = C x - A (B x) for a
+    # +-1 probe, one pass over A, B and C (HBM-bound), fp32 and fp64 accumulation
+    residual = None
+    if not args.no_residual:
+        x = torch.from_numpy(inputs.rademacher(n, inputs.seed_for(2, 95))).cuda()
+        rbytes = 4.0 * 3 * n * n
+        peak_gbs = peaks()[0]["hbm_gbs"]
+        scale = float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * n * n
+        residual = {"bytes": rbytes, "peak_gbs": peak_gbs}
+        for name, fp64 in (("fp32", False), ("fp64", True)):
+            rms = timed(torch, dist, world, lambda: fmm.fmm_residual(dA, dB, dC, x, fp64=fp64), min(args.steps, 20), 3)
+            r = fmm.fmm_residual(dA, dB, dC, x, fp64=fp64)
+            residual[name] = {"ms": round(rms, 4), "achieved_gbs": round(rbytes / rms / 1e6, 1),
+                              "frac": round(rbytes / rms / 1e6 / peak_gbs, 3),
+                              "max_abs_r_over_maxA_maxB_n2": float(r.abs().max().item()) / scale}
+
     classical = None
     if not args.no_classical:
         cplan = fmm.Plan(n, n, n, depth=0, precision=args.precision, leaf_tile=args.leaf_tile)
@@ -696,6 +713,7 @@ def main():
         "classical": classical,
         "speedup_vs_classical": round(value / classical["gflops"], 3) if classical else None,
         "split_precision": split,
+        "residual": residual,
         "phases": phases,
         "additions": additions,
         "roofline": roofline,

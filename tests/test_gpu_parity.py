@@ -195,13 +195,15 @@ def test_peel_blas_semantics(fmm):
 # --- residual check ------------------------------------------------------------
 
 @pytest.mark.parametrize("fp64", [0, 1])
-def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64):
+@pytest.mark.parametrize("m,k,n", [(700, 500, 600), (301, 203, 157)])
+def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64, m, k, n):
+    # (301, 203, 157): rows of A and C not 16-byte aligned (one column at a
+    # time) and column counts with a remainder of 4 in every pass
     import torch
-    m, k, n = 700, 500, 600
     A = I.small_int((m, k), 21, r=3)
     B = I.small_int((k, n), 22, r=3)
     Cx = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
-    Cx[123, 45] += 1.0
+    Cx[123, 45 % n] += 1.0
     x = I.rademacher(n, 23)
     dA, dB, dC, dx = (torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in (A, B, Cx, x))
     r = fmm.fmm_residual(dA, dB, dC, dx, fp64=bool(fp64))
@@ -210,6 +212,32 @@ def test_freivalds_residual_matches_oracle_and_detects_error(fmm, fp64):
     want = O.freivalds(A, B, Cx, x)
     assert np.array_equal(got, want)           # integer data: exact in both accumulations
     assert np.count_nonzero(got) == 1 and abs(got[123]) == 1.0
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_freivalds_residual_strided_views(fmm, fp64):
+    # row strides that are multiples of 4 with column counts that are not: the
+    # 16-byte path for the first columns of every row, one at a time for the rest
+    import torch
+    m, k, n = 257, 130, 99
+    A = I.small_int((m, k), 31, r=3)
+    B = I.small_int((k, n), 32, r=3)
+    Cx = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+    Cx[200, 98] -= 2.0
+    x = I.rademacher(n, 33)
+
+    def view(t, ld):
+        buf = torch.zeros((t.shape[0], ld), dtype=torch.float32, device="cuda")
+        buf[:, : t.shape[1]] = torch.from_numpy(t).cuda()
+        return buf[:, : t.shape[1]]
+
+    dA, dB, dC = view(A, 132), view(B, 100), view(Cx, 100)
+    assert dA.stride(0) == 132 and dB.stride(0) == 100
+    r = fmm.fmm_residual(dA, dB, dC, torch.from_numpy(x).cuda(), fp64=bool(fp64))
+    torch.cuda.synchronize()
+    got = r.cpu().numpy()
+    assert np.array_equal(got, O.freivalds(A, B, Cx, x))
+    assert np.count_nonzero(got) == 1 and abs(got[200]) == 2.0
 
 
 # --- split-precision leaves (BF16x3, FP16x3) ----------------------------------
