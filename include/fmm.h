@@ -156,8 +156,10 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
  * workspace (synchronously); fmm_batched_run then only launches kernels: one
  * batched transpose/copy launch, the pre-additions of the problems that
  * recurse, ONE persistent leaf launch over every leaf product of every problem
- * (longest tiles first), and the post-additions.  The operand pointers are
- * bound at plan time.  With out == NULL only *workspace_needed is set. */
+ * (longest tiles first), and the post-additions; FP16x3 first derives every
+ * problem's own power-of-two operand scales (two launches).  The operand
+ * pointers are bound at plan time.  With out == NULL only *workspace_needed is
+ * set.  Errors: UNSUPPORTED for opt->odd = PEEL or opt->algo = CLASSICAL. */
 typedef struct fmm_batched_s* fmm_batched_t;
 fmm_status_t fmm_batched_plan(fmm_batched_t* out, int count, const int64_t* M, const int64_t* N,
                               const int64_t* K, const float* const* A, const int64_t* lda,

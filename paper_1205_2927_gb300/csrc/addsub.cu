@@ -311,16 +311,49 @@ __global__ void absmax_kernel(const float* __restrict__ X, long long ld, long lo
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-__global__ void fp16_scale_kernel(const unsigned* mx, float bound_mult, float* scale) {
-    const int i = threadIdx.x;
-    if (i > 1) return;
-    const float m = __uint_as_float(mx[i]) * bound_mult;
-    if (!(m > 0.f) || !isfinite(m)) { scale[i] = 1.0f; return; }
+// Largest power of two s with m * s <= 2^14 (1 for m = 0 or not finite).
+__device__ __forceinline__ float fp16_scale_of(float m) {
+    if (!(m > 0.f) || !isfinite(m)) return 1.0f;
     int x;
     frexpf(m, &x);                   // m = f * 2^x, 0.5 <= f < 1
     int e = 14 - x;                  // largest e with m * 2^e <= 2^14
     e = max(-100, min(100, e));
-    scale[i] = ldexpf(1.0f, e);
+    return ldexpf(1.0f, e);
+}
+
+__global__ void fp16_scale_kernel(const unsigned* mx, float bound_mult, float* scale) {
+    const int i = threadIdx.x;
+    if (i > 1) return;
+    scale[i] = fp16_scale_of(__uint_as_float(mx[i]) * bound_mult);
+}
+
+// Batched maxima: one 32 x 128 block of one operand per CTA (the job found by
+// binary search on its first block), folded into the job's slot.
+__global__ void __launch_bounds__(256) batched_absmax_kernel(const AbsJob* __restrict__ jobs, int njobs) {
+    const long long t = blockIdx.x;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    const AbsJob J = jobs[lo];
+    const long long local = t - J.tile_begin;
+    const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 128;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < 32 * 128; i += 256) {
+        const long long r = r0 + (i >> 7), c = c0 + (i & 127);
+        if (r < J.rows && c < J.cols) m = fmaxf(m, fabsf(__ldg(J.src + r * J.lds + c)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(J.slot, __float_as_uint(m));
+}
+
+__global__ void batched_fp16_scale_kernel(const unsigned* __restrict__ maxima, const float* __restrict__ bound,
+                                          float* __restrict__ scales, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * count) return;
+    scales[i] = fp16_scale_of(__uint_as_float(maxima[i]) * bound[i >> 1]);
 }
 
 // Root pre-additions of the host-streamed schedule: the four quadrants are
@@ -1045,6 +1078,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const SplitJob* __re
         if (jobs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
     }
     const SplitJob J = jobs[lo];
+    const float sc = J.scale ? J.scale[J.transpose] : 1.0f;
     const long long local = t - J.tile_begin;
     const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 128;
     const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -1072,7 +1106,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const SplitJob* __re
             const int g = tid + 256 * j;
             const long long r = r0 + (g >> 5), c = c0 + 4 * (g & 31);
             // ld is a multiple of 8, so a group of 4 never crosses a row: padding columns get zeros
-            if (r < J.rows && c < J.cols) split_store<KIND>(J.dst, J.lo, r * J.ldd + c, v[j], 1.0f);
+            if (r < J.rows && c < J.cols) split_store<KIND>(J.dst, J.lo, r * J.ldd + c, v[j], sc);
         }
         return;
     }
@@ -1098,7 +1132,7 @@ __global__ void __launch_bounds__(256) batched_split_kernel(const SplitJob* __re
         const long long orow = c0 + a, ocol = r0 + q;
         if (orow < J.cols && ocol < J.rows) {
             const float4 v = make_float4(tile[q][a], tile[q + 1][a], tile[q + 2][a], tile[q + 3][a]);
-            split_store<KIND>(J.dst, J.lo, orow * J.ldd + ocol, v, 1.0f);
+            split_store<KIND>(J.dst, J.lo, orow * J.ldd + ocol, v, sc);
         }
     }
 }
@@ -1389,6 +1423,19 @@ cudaError_t launch_batched_split(const SplitJob* jobs, int njobs, long long tota
         case kSplitFP16: batched_split_kernel<kSplitFP16><<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs); break;
         default: batched_split_kernel<kSplitTF32><<<(unsigned)total_tiles, dim3(32, 8), 0, stream>>>(jobs, njobs);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_absmax(const AbsJob* jobs, int njobs, long long total_tiles, cudaStream_t stream) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    batched_absmax_kernel<<<(unsigned)total_tiles, 256, 0, stream>>>(jobs, njobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_fp16_scales(const unsigned* maxima, const float* bound, float* scales, int count,
+                                       cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    batched_fp16_scale_kernel<<<(unsigned)((2 * count + 255) / 256), 256, 0, stream>>>(maxima, bound, scales, count);
     return cudaGetLastError();
 }
 

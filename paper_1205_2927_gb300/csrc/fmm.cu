@@ -202,7 +202,8 @@ struct fmm_plan_s {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t hev[8] = {};
     // FP16x3: device operand scales {s_a, s_b} and reduction scratch, inside the status block
-    float* fp16_scale() const { return reinterpret_cast<float*>(status + 16); }
+    float* fp16_scale() const { return scale_override ? scale_override : reinterpret_cast<float*>(status + 16); }
+    float* scale_override = nullptr;   // batched sub-plans: the problem's own {s_a, s_b}
     unsigned* fp16_scratch() const { return status + 24; }
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -883,6 +884,14 @@ struct fmm_batched_s {
     int count = 0;
     int bn = 256, mode = kLeaf3xTF32, num_sms = 0;
     int pair = 0;                      // leaf tiles of 256 x 256 on CTA pairs (pre-split precisions)
+    // FP16x3: per-problem operand maxima, bounds (4^depth) and scales {s_a, s_b}
+    int fp16 = 0;
+    AbsJob* d_ajobs = nullptr;
+    int najobs = 0;
+    long long ajob_tiles = 0;
+    unsigned* d_absmax = nullptr;
+    float* d_bound = nullptr;
+    float* d_scales = nullptr;
     unsigned* status = nullptr;
     CUtensorMap* d_maps = nullptr;
     GemmGroup* d_groups = nullptr;
@@ -918,15 +927,16 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     b->status = cv.take<unsigned>(64);
     b->count = count;
     b->mode = leaf_mode(o.precision);
-    b->pre = o.precision == FMM_PREC_FP32 || o.precision == FMM_PREC_BF16X3;
+    b->fp16 = o.precision == FMM_PREC_FP16X3 ? 1 : 0;
+    b->pre = o.precision == FMM_PREC_FP32 || o.precision == FMM_PREC_BF16X3 || b->fp16;
     // leaf tile 512 (and the default 0): 256 x 256 tiles on CTA pairs for the
     // pre-split precisions (512 uneven products: 8.70 ms per replay against 9.10
     // on single CTAs); TF32 batched launches stay on single CTAs (128 x 256)
     b->pair = ((o.leaf_tile == 512 || o.leaf_tile == 0) && b->pre) ? 1 : 0;
     b->bn = (o.leaf_tile && o.leaf_tile != 512) ? o.leaf_tile : 256;
     if (b->pre) {
-        b->split_kind = o.precision == FMM_PREC_BF16X3 ? kSplitBF16 : kSplitTF32;
-        b->mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : kLeaf3xTF32P;
+        b->split_kind = o.precision == FMM_PREC_BF16X3 ? kSplitBF16 : b->fp16 ? kSplitFP16 : kSplitTF32;
+        b->mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : b->fp16 ? kLeafFP16x3P : kLeaf3xTF32P;
     }
     const size_t es = b->split_kind == kSplitTF32 ? 4 : 2;
     // per-problem depth and resource counts
@@ -948,6 +958,17 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     b->d_groups = cv.take<GemmGroup>(total_groups > 0 ? total_groups : 1);
     b->d_jobs = cv.take<CopyJob>(total_jobs > 0 ? total_jobs : 1);
     b->d_sjobs = cv.take<SplitJob>(total_jobs > 0 ? total_jobs : 1);
+    std::vector<AbsJob> ajobs;
+    std::vector<float> bound;
+    if (b->fp16) {
+        b->d_ajobs = cv.take<AbsJob>(2 * (size_t)(count > 0 ? count : 1));
+        b->d_absmax = cv.take<unsigned>(2 * (size_t)(count > 0 ? count : 1));
+        b->d_bound = cv.take<float>((size_t)(count > 0 ? count : 1));
+        b->d_scales = cv.take<float>(2 * (size_t)(count > 0 ? count : 1));
+        bound.assign(count > 0 ? count : 1, 1.0f);
+    }
+    // the problem's scales (FP16x3), or null
+    auto scale_of = [&](int i) -> float* { return b->fp16 && b->d_scales ? b->d_scales + 2 * i : nullptr; };
     std::vector<SplitJob> sjobs;
     std::vector<CUtensorMap> maps(total_maps > 0 ? total_maps : 1);
     std::vector<GemmGroup> groups(total_groups > 0 ? total_groups : 1);
@@ -956,6 +977,12 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     for (int i = 0; i < count; ++i) {
         const int d = b->depth[i];
         if (d < 0) continue;
+        if (b->fp16 && ws) {
+            // operand magnitudes of the leaves are bounded by 4^depth times the problem's
+            bound[i] = (float)(1LL << (2 * d));
+            ajobs.push_back(AbsJob{A[i], lda[i], M[i], K[i], b->d_absmax + 2 * i, 0, (int)((K[i] + 127) / 128)});
+            ajobs.push_back(AbsJob{B[i], ldb[i], K[i], N[i], b->d_absmax + 2 * i + 1, 0, (int)((N[i] + 127) / 128)});
+        }
         if (d == 0 && b->pre) {
             const long long ld = rup(K[i], 128 / (long long)es);   // 128-byte row pitch
             void* ah = cv.take<char>((size_t)M[i] * ld * es);
@@ -963,8 +990,8 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             void* bh = cv.take<char>((size_t)N[i] * ld * es);
             void* bl = cv.take<char>((size_t)N[i] * ld * es);
             if (!ws) continue;
-            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], ah, al, ld, 0, (int)((K[i] + 127) / 128), 0});
-            sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 127) / 128), 1});
+            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], ah, al, ld, 0, (int)((K[i] + 127) / 128), 0, scale_of(i)});
+            sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 127) / 128), 1, scale_of(i)});
             fmm_status_t s;
             const int kd = b->split_kind;
             const bool wide = b->pair != 0;              // pair: 128-byte rows, 128 rows of B per CTA
@@ -979,6 +1006,7 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             G.C = C[i]; G.ldc = ldc[i]; G.alpha = alpha[i]; G.beta = beta[i];
             G.map_a = nm; G.map_a_lo = nm + 1; G.map_b = nm + 2; G.map_b_lo = nm + 3;
             G.vec_ok = ((reinterpret_cast<uintptr_t>(C[i]) & 15) == 0 && ldc[i] % 4 == 0) ? 1 : 0;
+            G.scale = scale_of(i);
             nm += 4;
         } else if (d == 0) {
             const long long ldt = rup(K[i], 4);
@@ -1024,10 +1052,13 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             if (!q) return FMM_ERR_OOM;
             layout(q, sub_ws, nullptr);
             q->status = b->status;
+            q->scale_override = scale_of(i);
             b->subs.push_back(q);
             b->sub_problem.push_back(i);
             fmm_status_t s;
+            const int ng0 = ng;
             if ((s = winograd_leaf_groups(q, maps.data(), nm, groups.data(), ng)) != FMM_OK) return s;
+            for (int g = ng0; g < ng; ++g) groups[g].scale = scale_of(i);
         }
     }
     if (needed) *needed = align_up(cv.off, 256);
@@ -1057,6 +1088,18 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     }
     b->njobs = (int)(b->pre ? sjobs.size() : jobs.size());
     b->job_tiles = jt;
+    if (b->fp16) {
+        long long at = 0;
+        for (auto& J : ajobs) {
+            J.tile_begin = at;
+            at += ((J.rows + 31) / 32) * (long long)J.tiles_c;
+        }
+        b->najobs = (int)ajobs.size();
+        b->ajob_tiles = at;
+        if (!ajobs.empty())
+            FMM_CUDA(cudaMemcpy(b->d_ajobs, ajobs.data(), sizeof(AbsJob) * ajobs.size(), cudaMemcpyHostToDevice));
+        FMM_CUDA(cudaMemcpy(b->d_bound, bound.data(), sizeof(float) * bound.size(), cudaMemcpyHostToDevice));
+    }
     if (!sjobs.empty())
         FMM_CUDA(cudaMemcpy(b->d_sjobs, sjobs.data(), sizeof(SplitJob) * sjobs.size(), cudaMemcpyHostToDevice));
     FMM_CUDA(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * (nm > 0 ? nm : 1), cudaMemcpyHostToDevice));
@@ -1085,8 +1128,7 @@ fmm_status_t batched_check(int count, const int64_t* M, const int64_t* N, const 
     if (opt) {
         fmm_status_t s = check_opts(opt);
         if (s != FMM_OK) return s;
-        if (opt->odd != FMM_ODD_PAD || opt->precision == FMM_PREC_FP16X3 || opt->algo == FMM_ALGO_CLASSICAL)
-            return FMM_ERR_UNSUPPORTED;
+        if (opt->odd != FMM_ODD_PAD || opt->algo == FMM_ALGO_CLASSICAL) return FMM_ERR_UNSUPPORTED;
     }
     (void)A; (void)B; (void)C;
     return FMM_OK;
@@ -1555,6 +1597,12 @@ fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
     if (!b) return FMM_ERR_INVALID_ARG;
     cudaStream_t stream = (cudaStream_t)stream_;
     fmm_status_t s;
+    if (b->fp16 && b->count > 0) {   // per-problem operand scales first: the splits and sub-plans apply them
+        FMM_CUDA(cudaMemsetAsync(b->d_absmax, 0, 2 * sizeof(unsigned) * (size_t)b->count, stream));
+        FMM_CUDA(launch_batched_absmax(b->d_ajobs, b->najobs, b->ajob_tiles, stream));
+        FMM_CUDA(launch_batched_fp16_scales(b->d_absmax, b->d_bound, b->d_scales, b->count, stream));
+        b->launches += 2;
+    }
     if (b->njobs > 0) {
         if (b->pre) FMM_CUDA(launch_batched_split(b->d_sjobs, b->njobs, b->job_tiles, b->split_kind, stream));
         else FMM_CUDA(launch_batched_copy(b->d_jobs, b->njobs, b->job_tiles, stream));

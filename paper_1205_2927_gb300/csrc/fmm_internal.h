@@ -141,9 +141,25 @@ struct SplitJob {
     long long tile_begin;   // first 32 x 128 block of the job in the launch
     int tiles_c;            // 128-column blocks per 32-row band of the source
     int transpose;
+    const float* scale;     // FP16x3: the problem's device {s_a, s_b} (the job uses scale[transpose]), or null
 };
 cudaError_t launch_batched_split(const SplitJob* jobs, int njobs, long long total_tiles, int kind,
                                  cudaStream_t stream);
+// FP16x3 in a batched launch: the largest |x| of every operand (rows x cols,
+// row stride lds) is folded into its problem's slot, one launch over 32 x 128
+// blocks of all operands; then every problem's scales {s_a, s_b} from its two
+// maxima times its bound (4^depth), by the rule of launch_fp16_scales.
+struct AbsJob {
+    const float* src;
+    long long lds;
+    long long rows, cols;
+    unsigned* slot;         // float bits of the running maximum (starts at 0)
+    long long tile_begin;
+    int tiles_c;
+};
+cudaError_t launch_batched_absmax(const AbsJob* jobs, int njobs, long long total_tiles, cudaStream_t stream);
+cudaError_t launch_batched_fp16_scales(const unsigned* maxima, const float* bound, float* scales, int count,
+                                       cudaStream_t stream);
 // FP16x3 operand scales: scale[0] = 2^e_a, scale[1] = 2^e_b with the largest
 // e such that bound_mult * max|X| * 2^e <= 2^14 (1 when X is all zero); the
 // maxima are taken over the M x K / K x N operands (any leading dimension).

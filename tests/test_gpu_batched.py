@@ -33,7 +33,7 @@ def _upload(probs):
     return As, Bs, Cs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3", "tf32"])
 @pytest.mark.parametrize("cutoff,bn", [(4096, 256), (64, 256), (64, 128), (4096, 512), (64, 512)])
 def test_batched_bit_exact_small_int(F, cutoff, bn, prec):
     import torch
@@ -69,6 +69,34 @@ def test_batched_alpha_beta_and_float_bound(F, bn):
         ref = O.gemm(0.5, A, B, 2.0, c0)
         err = np.max(np.abs(Cd.cpu().numpy() - ref)) / (np.abs(A).max() * np.abs(B).max() * A.shape[1])
         assert err <= 2e-6
+
+
+@pytest.mark.parametrize("bn", [256, 512])
+def test_batched_fp16x3_scales_per_problem(F, bn):
+    # operands of very different magnitudes in one launch: each problem gets its
+    # own power-of-two scales (a shared scale would push the small problems'
+    # lo halves below fp16's range); the recursing problems included
+    import torch
+    shapes = I.batched_shapes(24, 9600, lo=64, hi=900, multiple=4)
+    probs, As, Bs, Cs = [], [], [], []
+    for i, (m, k, n) in enumerate(shapes):
+        s = 4.0 ** ((i % 7) - 3)               # magnitudes from 2^-6 to 2^6
+        A, B = I.operands(m, k, n, 9700 + i, "normal")
+        A = (A * s).astype(np.float32)
+        B = (B / s).astype(np.float32)
+        probs.append((A, B))
+        As.append(torch.from_numpy(A).cuda())
+        Bs.append(torch.from_numpy(B).cuda())
+        Cs.append(torch.full((m, n), float("nan"), device="cuda"))
+    bp = F.BatchedPlan(As, Bs, Cs, cutoff=128, leaf_tile=bn, precision="fp16x3")
+    assert max(bp.info()["depths"]) >= 1
+    bp.run()
+    torch.cuda.synchronize()
+    for (A, B), Cd in zip(probs, Cs):
+        ref = O.classical(A, B)
+        err = np.max(np.abs(Cd.cpu().numpy() - ref)) / (np.abs(A).max() * np.abs(B).max() * A.shape[1])
+        assert err <= 2e-6, err
+    bp.close()
 
 
 def test_batched_graph_capture_replay(F):
@@ -114,7 +142,7 @@ def test_one_shot_gemm_batched_and_unsupported_forms(F):
         ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
         assert np.array_equal(Cd.cpu().numpy(), ref)
     # forms the batched path rejects before any device work
-    for kw in ({"precision": "fp16x3"}, {"odd": "peel"}, {"algo": "classical"}):
+    for kw in ({"odd": "peel"}, {"algo": "classical"}):
         with pytest.raises(F.FmmError) as e:
             F.fmm_gemm_batched(As, Bs, Cs, **kw)
         assert e.value.status == 6
