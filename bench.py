@@ -386,7 +386,8 @@ def wl_split(args):
 def wl_batched(args):
     """512 independent products, M, K, N log-uniform in [128, 4096] (multiples of 4),
     U[-1,1]; one persistent leaf launch per replay of a CUDA graph; the leaf tile and the
-    per-problem depth cut-off are tuned by timing the whole batch."""
+    per-problem depth cut-off are tuned by timing the whole batch (`--precision` selects
+    the leaves: fp32 = 3xTF32, tf32, bf16x3, fp16x3)."""
     import numpy as np
     import torch
     from paper_1205_2927_gb300 import fmm, inputs
@@ -399,7 +400,7 @@ def wl_batched(args):
     t_tune0 = time.perf_counter()
     for bn in (128, 256, 512):
         for cutoff in (1024, 2048, 8192):
-            bp = fmm.BatchedPlan(As, Bs, Cs, leaf_tile=bn, cutoff=cutoff)
+            bp = fmm.BatchedPlan(As, Bs, Cs, leaf_tile=bn, cutoff=cutoff, precision=args.precision)
             s = torch.cuda.Stream()
             s.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(s):
@@ -411,7 +412,8 @@ def wl_batched(args):
                 bp.run(torch.cuda.current_stream())
             ms = event_ms(torch, g.replay, 20, 3)
             info = bp.info()
-            rec = {"workload": "batched512", "leaf_tile": bn, "cutoff": cutoff, "graph_replay_ms": round(ms, 3),
+            rec = {"workload": "batched512", "precision": args.precision, "leaf_tile": bn, "cutoff": cutoff,
+                   "graph_replay_ms": round(ms, 3),
                    "gflops": round(flops / ms / 1e6, 1), "total_flops": flops,
                    "recursing_problems": int(sum(1 for d in info["depths"] if d > 0)),
                    "leaf_tiles": info["total_tiles"]}
@@ -431,7 +433,8 @@ def wl_batched(args):
         ref = A_h.astype(np.float64) @ B_h.astype(np.float64)
         errs.append(float(np.max(np.abs(Cs[i].cpu().numpy() - ref))) /
                     (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * A_h.shape[1]))
-    emit(args, {"workload": "batched512_best", "leaf_tile": bn, "cutoff": cutoff, "graph_replay_ms": round(ms, 3),
+    emit(args, {"workload": "batched512_best", "precision": args.precision, "leaf_tile": bn, "cutoff": cutoff,
+                "graph_replay_ms": round(ms, 3),
                 "gflops": round(flops / ms / 1e6, 1), "tuning_s": round(tune_s, 2), "max_error_sampled": max(errs),
                 "launches_per_replay": "1 batched copy + pre/post of recursing problems + 1 persistent leaf launch"})
 

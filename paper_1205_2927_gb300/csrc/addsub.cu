@@ -328,8 +328,10 @@ __global__ void fp16_scale_kernel(const unsigned* mx, float bound_mult, float* s
 }
 
 // Batched maxima: one 32 x 128 block of one operand per CTA (the job found by
-// binary search on its first block), folded into the job's slot.
+// binary search on its first block); 16-byte loads when the rows allow, every
+// load issued before the first compare; one atomic per CTA into the job's slot.
 __global__ void __launch_bounds__(256) batched_absmax_kernel(const AbsJob* __restrict__ jobs, int njobs) {
+    __shared__ float warp_max[8];
     const long long t = blockIdx.x;
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
@@ -339,14 +341,36 @@ __global__ void __launch_bounds__(256) batched_absmax_kernel(const AbsJob* __res
     const AbsJob J = jobs[lo];
     const long long local = t - J.tile_begin;
     const long long r0 = (local / J.tiles_c) * 32, c0 = (local % J.tiles_c) * 128;
-    float m = 0.f;
-    for (int i = threadIdx.x; i < 32 * 128; i += 256) {
-        const long long r = r0 + (i >> 7), c = c0 + (i & 127);
-        if (r < J.rows && c < J.cols) m = fmaxf(m, fabsf(__ldg(J.src + r * J.lds + c)));
+    const bool vec = (reinterpret_cast<uintptr_t>(J.src) & 15) == 0 && (J.lds & 3) == 0;
+    float4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int g = threadIdx.x + 256 * j;   // row g / 32 of the block, columns 4 (g % 32) .. + 3
+        const long long r = r0 + (g >> 5), c = c0 + 4 * (g & 31);
+        v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r >= J.rows || c >= J.cols) continue;
+        const float* src = J.src + r * J.lds + c;
+        if (vec && c + 3 < J.cols) {
+            v[j] = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+            v[j].x = __ldg(src);
+            if (c + 1 < J.cols) v[j].y = __ldg(src + 1);
+            if (c + 2 < J.cols) v[j].z = __ldg(src + 2);
+            if (c + 3 < J.cols) v[j].w = __ldg(src + 3);
+        }
     }
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m = fmaxf(fmaxf(m, fmaxf(fabsf(v[j].x), fabsf(v[j].y))), fmaxf(fabsf(v[j].z), fabsf(v[j].w)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(J.slot, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, warp_max[w]);
+        atomicMax(J.slot, __float_as_uint(m));
+    }
 }
 
 __global__ void batched_fp16_scale_kernel(const unsigned* __restrict__ maxima, const float* __restrict__ bound,
