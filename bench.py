@@ -511,6 +511,16 @@ def cublas_tf32_tflops(torch, n=8192, reps=10):
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
+def max_over_ranks(torch, dist, world, value, device):
+    """The largest of every rank's `value` (the step time of the slowest
+    replica); the value itself with one rank."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def timed(torch, dist, world, fn, steps, warmup, clocks=None):
     for _ in range(warmup):
         fn()
@@ -529,12 +539,7 @@ def timed(torch, dist, world, fn, steps, warmup, clocks=None):
         clocks.window = (t0, time.perf_counter())
     if world > 1:
         dist.barrier()
-    ms = s.elapsed_time(e) / steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return max_over_ranks(torch, dist, world, s.elapsed_time(e) / steps, "cuda")
 
 
 def main():
