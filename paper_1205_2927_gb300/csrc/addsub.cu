@@ -300,15 +300,39 @@ __global__ void fill_kernel(float* p, size_t n, unsigned seed) {
 
 // max |x| over a rows x cols matrix, folded into *out (float bits; non-negative
 // floats order like unsigned integers)
-__global__ void absmax_kernel(const float* __restrict__ X, long long ld, long long rows, long long cols,
-                              unsigned* out) {
+// max |X| over a rows x cols operand (row stride ld): rows grid-strided over
+// blockIdx.y, columns over blockIdx.x; 16-byte loads when the rows allow;
+// one atomic per block.
+__global__ void __launch_bounds__(256) absmax_kernel(const float* __restrict__ X, long long ld, long long rows,
+                                                     long long cols, unsigned* out) {
+    __shared__ float warp_max[8];
+    const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ld & 3) == 0;
+    const long long step = (long long)gridDim.x * blockDim.x;
     float m = 0.f;
-    for (long long r = blockIdx.y; r < rows; r += gridDim.y)
-        for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += (long long)gridDim.x * blockDim.x)
-            m = fmaxf(m, fabsf(X[r * ld + c]));
+    for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+        const float* xr = X + r * ld;
+        if (vec) {
+            const long long groups = cols >> 2;
+            for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += step) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(xr) + g);
+                m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            }
+            for (long long c = (groups << 2) + (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += step)
+                m = fmaxf(m, fabsf(__ldg(xr + c)));
+        } else {
+            for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += step)
+                m = fmaxf(m, fabsf(__ldg(xr + c)));
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, warp_max[w]);
+        atomicMax(out, __float_as_uint(m));
+    }
 }
 
 // Largest power of two s with m * s <= 2^14 (1 for m = 0 or not finite).
