@@ -21,10 +21,10 @@ namespace {
 // partial sums; the last cols % 4 columns, or every column of unaligned rows,
 // go one at a time.  Warp sums, then the 8 warp sums in a fixed order.  One
 // row per block keeps the grid many waves deep (16384 rows: 13.5 waves).
-template <typename Acc, typename Vec>
+template <typename Acc, typename Vec, typename Out>
 __global__ void __launch_bounds__(256) rowdot_kernel(const float* __restrict__ X, long long ld, long long rows,
                                                      long long cols, const Vec* __restrict__ v,
-                                                     double* __restrict__ out, const double* __restrict__ sub,
+                                                     Out* __restrict__ out, const double* __restrict__ sub,
                                                      int vec4) {
     __shared__ Acc warp_sum[8];
     const long long row = blockIdx.x;
@@ -64,25 +64,29 @@ __global__ void __launch_bounds__(256) rowdot_kernel(const float* __restrict__ X
         Acc s = warp_sum[0];
 #pragma unroll
         for (int w = 1; w < 8; ++w) s += warp_sum[w];
-        out[row] = sub ? (double)s - sub[row] : (double)s;
+        if (sub) out[row] = (Out)((double)s - sub[row]);
+        else out[row] = (Out)s;
     }
 }
 
 inline int aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0 ? 1 : 0; }
 
+// y = B x ; z = A y ; r = C x - z.  y is kept in the accumulation type: an
+// fp32 sum is exactly representable either way, and a float y keeps the
+// middle pass off the FP64 pipe (a double-to-float conversion per element).
 template <typename Acc>
 cudaError_t residual_impl(long long M, long long N, long long K, const float* A, long long lda, const float* B,
-                          long long ldb, const float* C, long long ldc, const float* x, double* r, double* y,
+                          long long ldb, const float* C, long long ldc, const float* x, double* r, double* y_ws,
                           double* z, cudaStream_t s) {
-    // y = B x ; z = A y ; r = C x - z
+    Acc* y = reinterpret_cast<Acc*>(y_ws);   // K entries (the workspace holds K doubles)
     const int vx = aligned16(x), vy = aligned16(y);
     if (K > 0)
-        rowdot_kernel<Acc, float><<<(unsigned)K, 256, 0, s>>>(B, ldb, K, N, x, y, nullptr,
-                                                                          vx & aligned16(B) & (ldb % 4 == 0));
-    rowdot_kernel<Acc, double><<<(unsigned)M, 256, 0, s>>>(A, lda, M, K, y, z, nullptr,
-                                                                       vy & aligned16(A) & (lda % 4 == 0));
-    rowdot_kernel<Acc, float><<<(unsigned)M, 256, 0, s>>>(C, ldc, M, N, x, r, z,
-                                                                      vx & aligned16(C) & (ldc % 4 == 0));
+        rowdot_kernel<Acc, float, Acc><<<(unsigned)K, 256, 0, s>>>(B, ldb, K, N, x, y, nullptr,
+                                                                   vx & aligned16(B) & (ldb % 4 == 0));
+    rowdot_kernel<Acc, Acc, double><<<(unsigned)M, 256, 0, s>>>(A, lda, M, K, y, z, nullptr,
+                                                                vy & aligned16(A) & (lda % 4 == 0));
+    rowdot_kernel<Acc, float, double><<<(unsigned)M, 256, 0, s>>>(C, ldc, M, N, x, r, z,
+                                                                  vx & aligned16(C) & (ldc % 4 == 0));
     return cudaGetLastError();
 }
 
