@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "single1024", "sweep", "large", "rmul", "split", "batched", "planner"],
+                    choices=["square", "single1024", "sweep", "large", "rmul", "split", "batched", "planner",
+                             "residual"],
                     help="square: the headline line; the others measure the other configurations")
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     return ap.parse_args()
@@ -439,6 +440,23 @@ def wl_batched(args):
                 "launches_per_replay": "1 batched copy + pre/post of recursing problems + 1 persistent leaf launch"})
 
 
+def wl_residual(args):
+    """The Freivalds residual check alone at n x n (A, B, C U[-1,1], a +-1 probe):
+    one pass over A, B and C per call, fp32 and fp64 accumulation; CUDA events
+    over 10 calls after 2 warm-ups."""
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    n = args.n
+    A, B, C = (torch.from_numpy(inputs.uniform((n, n), inputs.seed_for(5, i))).cuda() for i in range(3))
+    x = torch.from_numpy(inputs.rademacher(n, inputs.seed_for(5, 3))).cuda()
+    nbytes = 4.0 * 3 * n * n
+    peak = peaks()[0]["hbm_gbs"]
+    for name, fp64 in (("fp32", False), ("fp64", True)):
+        ms = event_ms(torch, lambda: fmm.fmm_residual(A, B, C, x, fp64=fp64), 10, 2)
+        emit(args, {"workload": "residual", "n": n, "accumulation": name, "ms": round(ms, 4),
+                    "achieved_gbs": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 3)})
+
+
 def wl_planner(args):
     """Learned planner: ~20k candidate timings on shapes of the other configurations,
     network trained on the GPU, plans picked for 1000 unseen shapes; compared with
@@ -483,7 +501,7 @@ def wl_planner(args):
 
 WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "large": wl_large, "rmul": wl_rmul, "split": wl_split,
              "batched": wl_batched,
-             "planner": wl_planner}
+             "planner": wl_planner, "residual": wl_residual}
 
 def cublas_tf32_tflops(torch, n=8192, reps=10):
     """TF32 tensor-core rate of the vendor library on this GPU (a live
