@@ -115,30 +115,38 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.reader.join(timeout=5)
-        lines, where = self.lines, "whole run"
-        if self.window:
-            inside = [x for x in lines if self.window[0] <= x[0] <= self.window[1]]
-            if inside:
-                lines, where = inside, "timed region"
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for _, line in lines:
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "samples_in": where,
-                "reasons": sorted(reasons)}
+        return summarize_clock_samples(self.lines, self.window)
+
+
+def summarize_clock_samples(lines, window):
+    """Median SM clock, maximum SM clock and the throttle reasons seen, from
+    (host time, nvidia-smi csv line) samples (the query of Clocks.Q); only the
+    samples inside `window` (host-time bounds of the timed region) when there
+    are any.  None without a usable sample."""
+    where = "whole run"
+    if window:
+        inside = [x for x in lines if window[0] <= x[0] <= window[1]]
+        if inside:
+            lines, where = inside, "timed region"
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for _, line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+            "samples_in": where,
+            "reasons": sorted(reasons)}
 
 
 def source_sha(path):
@@ -146,10 +154,10 @@ def source_sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic(kernel_file, workload_key):
+def ncu_traffic(kernel_file, workload_key, path=None):
     """Per-launch DRAM bytes of the leaf kernel from the committed ncu summary,
     valid only while the kernel source is the one that was profiled."""
-    path = os.path.join(ROOT, "profiles", "leaf_gemm_traffic.json")
+    path = path or os.path.join(ROOT, "profiles", "leaf_gemm_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
