@@ -72,6 +72,19 @@ def test_workspace_query_grows_with_depth(F):
     assert sizes[1] >= 21 * q
 
 
+@pytest.mark.parametrize("n,d,prec,es", [(16384, 3, "fp32", 4), (16384, 2, "fp32", 4), (8192, 3, "bf16x3", 2),
+                                          (4096, 0, "fp32", 4)])
+def test_workspace_closed_forms(F, n, d, prec, es):
+    # the split planes (hi and lo, both sides, every leaf) plus the leaf
+    # products are the whole workspace, apart from the status word and the
+    # tile-scheduling area (< 256 KB): no transposed copies or middle levels
+    need = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512)
+    leaves, h = 7 ** d, n >> d
+    planes = 2 * 2 * leaves * h * h * es
+    products = leaves * h * h * 4 if d > 0 else 0
+    assert 0 <= need - planes - products < 256 * 1024, need - planes - products
+
+
 def test_workspace_query_pads_to_level_granule(F):
     # 1000 at depth 2 pads to a multiple of 16: 1008
     s = _query(F, 1000, 1000, 1000, depth=2)
