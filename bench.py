@@ -55,6 +55,8 @@ def parse():
                              "residual"],
                     help="square: the headline line; the others measure the other configurations")
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
+    ap.add_argument("--model-out", default=None,
+                    help="planner workload: write the trained cost model to this file")
     return ap.parse_args()
 
 
@@ -171,29 +173,62 @@ def ncu_traffic(kernel_file, workload_key, path=None):
 
 # ---------------------------------------------------------------------------------- oracle legs
 
-def cpu_oracle_gflops(n=2048, depth=3, min_seconds=8.0, max_reps=50):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def cpu_threads():
+    """Threads the oracle's BLAS calls use: the cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_oracle_headline(A, B, depth, rows=64):
+    """The oracle at the headline configuration: one fp32 Winograd call (O2, numpy,
+    the bench's depth) on the full n x n operands, and the float64 classical
+    definition (O1) on `rows` sampled rows, both timed on the host cores."""
     import numpy as np
     from oracle import fmm_oracle as O
-    from paper_1205_2927_gb300 import inputs as I
-    A, B = I.operands(n, n, n, I.seed_for(2, 0))
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        O.winograd(A, B, depth, "pad")
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= min_seconds or reps >= max_reps:
-            break
-    return {"value": round(2.0 * n ** 3 * reps / el / 1e9, 2), "unit": "GFLOPS", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"fp32 Winograd oracle (numpy, depth {depth}) on n={n}, U[-1,1], {reps} calls in {el:.1f} s"}
+    n = A.shape[0]
+    t0 = time.perf_counter()
+    O.winograd(A, B, depth, "pad")
+    t_w = time.perf_counter() - t0
+    r = np.random.default_rng(7).choice(n, size=rows, replace=False)
+    t0 = time.perf_counter()
+    O.classical_rows(A, B, r)
+    t_c = time.perf_counter() - t0
+    return {"value": round(2.0 * n ** 3 / t_w / 1e9, 2), "unit": "GFLOPS", "cores": cpu_threads(),
+            "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"one fp32 Winograd oracle call (numpy, depth {depth}) on the full n={n} operands "
+                      f"in {t_w:.1f} s; float64 classical definition on {rows} sampled rows in {t_c:.2f} s "
+                      f"({2.0 * rows * n * n / t_c / 1e9:.1f} GFLOPS)"}
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores.  Each step is a bounded sample
+    of the headline workload: one of the seven root products of the n x n,
+    depth-3 call, i.e. an (n/2)^3 fp32 Winograd product at depth 2; throughput is
+    its effective 2 (n/2)^3 / t."""
     if rank != 0:
         return
-    n = 2048
-    depth = 3
-    import numpy as np  # noqa: F401
+    n = max(args.n // 2, 2)
+    depth = 2
     from oracle import fmm_oracle as O
     from paper_1205_2927_gb300 import inputs as I
     A, B = I.operands(n, n, n, I.seed_for(2, 0))
@@ -204,14 +239,15 @@ def run_reference(args, rank, world):
         O.winograd(A, B, depth, "pad")
     el = time.perf_counter() - t0
     val = 2.0 * n ** 3 * args.steps / el / 1e9
-    sample = f"fp32 Winograd oracle (numpy, depth {depth}) on n={n} per step (bounded sample of the n={args.n} workload)"
+    sample = (f"fp32 Winograd oracle (numpy) on one root product of the n={args.n} depth-3 call per step: "
+              f"n={n}, depth {depth}")
     line = {"impl": "reference", "metric": "effective GFLOPS (2MNK/s) Winograd vs classical GEMM on 1 GB300 at stated error",
             "value": round(val, 2), "unit": "GFLOPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"winograd_fp32_square_n{args.n}", "n": args.n, "sample_n": n, "depth": depth},
-            "cpu_baseline": {"value": round(val, 2), "unit": "GFLOPS", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": f"winograd_fp32_square_n{args.n}", "n": args.n, "sample_n": n, "depth": 3},
+            "cpu_baseline": {"value": round(val, 2), "unit": "GFLOPS", "cores": cpu_threads(), "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": round(val, 2), "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -486,8 +522,8 @@ def wl_planner(args):
     t0 = time.perf_counter()
     params, mean, std, losses = PL.train(X, y, steps=3000, lr=3e-3)
     t_train = time.perf_counter() - t0
-    PL.save(os.path.join(ROOT, "gpurun_out", "cost_model.bin") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-            else "/tmp/cost_model.bin", params, mean, std)
+    if args.model_out:
+        PL.save(args.model_out, params, mean, std)
     PL.register(params, mean, std)
     t0 = time.perf_counter()
     test = PL.collect(test_shapes, reps=1, seed=6)
@@ -535,6 +571,19 @@ def cublas_tf32_tflops(torch, n=8192, reps=10):
         return 2.0 * n ** 3 / (statistics.median(ts) * 1e-3) / 1e12
     finally:
         torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def tensor_peak(fmm, gpu_index, kind="tf32", runs=3, batches=30000):
+    """The project's tensor-pipe probe (fmm_tensor_peak), best of `runs`, with
+    the SM clock sampled while the probe ran."""
+    clk = Clocks(gpu_index)
+    clk.start()
+    t0 = time.perf_counter()
+    best = max(fmm.fmm_tensor_peak(kind, batches, seed=r + 1)[0] for r in range(runs))
+    clk.window = (t0, time.perf_counter())
+    c = clk.stop() or {}
+    return {"tflops": best, "kind": f"kind::{kind}" if kind == "tf32" else "kind::f16 (bf16)",
+            "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")}
 
 
 def max_over_ranks(torch, dist, world, value, device):
@@ -689,19 +738,25 @@ def main():
     leaf_flops = tc_products * 2.0 * leaf_count * float(leaf_dim) ** 3
     leaf_ms = prof["leaf_ms"] / max(prof["calls"], 1)
     achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
-    # the leaf launch is timed alone (events around that launch only): burst peak;
-    # the fraction against the sustained (power-capped) peak is reported beside it
-    peak_tf32 = pk["bf16_tflops"] * TF32_OVER_BF16
-    peak_tf32_sus = pk["bf16_tflops_sustained"] * TF32_OVER_BF16
+    # peak: the project's own tensor-pipe probe (fmm_tensor_peak: back-to-back
+    # tcgen05.mma of the leaf kernel's shape on shared-memory tiles), best of 3
+    # runs with the SM clock sampled while it ran; the leaf launch is timed alone
+    # (events around that launch only), so the burst figure is its ceiling
+    probe = tensor_peak(fmm, local, "tf32" if args.precision in ("fp32", "tf32") else "bf16")
+    peak_tc = probe["tflops"]
+    peak_nominal = pk["bf16_tflops"] * (TF32_OVER_BF16 if args.precision in ("fp32", "tf32") else 1.0)
     traffic = ncu_traffic(os.path.join(ROOT, "paper_1205_2927_gb300", "csrc", "leaf_gemm.cu"),
                           f"n{n}_d{depth}_bn{bn}_{args.precision}")
     kname = "leaf_gemm_pair_kernel (cta_group::2, 256x256 tiles)" if bn == 512 else f"leaf_gemm_kernel (128x{bn} tiles)"
     roofline = {"bound": "tensor", "kernel": kname + (" tcgen05 kind::tf32, pre-split raw/lo planes" if args.precision == "fp32"
                                                       else f" {args.precision}"),
-                "achieved": round(achieved, 1), "peak": round(peak_tf32, 1), "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tf32, 3), "traffic": traffic,
-                "peak_source": f"{pk_kind} bf16 burst {pk['bf16_tflops']} x nominal tf32/bf16 ratio 1.1/2.25",
-                "frac_of_sustained": round(achieved / peak_tf32_sus, 3),
+                "achieved": round(achieved, 1), "peak": round(peak_tc, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tc, 3), "traffic": traffic,
+                "peak_source": "measured: tcgen05 issue-rate probe (fmm_tensor_peak), "
+                               f"{probe['kind']} M=256 N=256 CTA pairs, best of 3 runs",
+                "peak_probe_sm_mhz": probe.get("sm_mhz"),
+                "peak_nominal_ratio": round(peak_nominal, 1),
+                "peak_nominal_ratio_source": f"{pk_kind} bf16 burst {pk['bf16_tflops']} x nominal tf32/bf16 1.1/2.25",
                 "work": f"{tc_products} TF32 products x 2*{leaf_count}*{leaf_dim}^3 flops per launch",
                 "leaf_ms_per_launch": round(leaf_ms, 3)}
     if args.precision in ("fp32", "tf32"):
@@ -723,15 +778,17 @@ def main():
     # end-to-end bound of the schedule: leaf work at the measured TF32 rate plus
     # the addition bytes at the measured HBM bandwidth, against the measured step
     if roofline.get("cublas_tf32_tflops"):
-        t_star = (leaf_flops / (roofline["cublas_tf32_tflops"] * 1e12)
-                  + (phase_bytes["pre_bytes"] + phase_bytes["post_bytes"]) / (pk["hbm_gbs"] * 1e9)) * 1e3
+        add_s = (phase_bytes["pre_bytes"] + phase_bytes["post_bytes"]) / (pk["hbm_gbs"] * 1e9)
+        t_star = (leaf_flops / (peak_tc * 1e12) + add_s) * 1e3
+        t_star_cublas = (leaf_flops / (roofline["cublas_tf32_tflops"] * 1e12) + add_s) * 1e3
         additions["bound_ms"] = {"t_star": round(t_star, 3), "measured": round(ms, 3),
                                  "t_star_over_measured": round(t_star / ms, 3),
-                                 "model": "leaf flops / cuBLAS TF32 rate + addition bytes / HBM copy bandwidth"}
+                                 "t_star_cublas_tf32": round(t_star_cublas, 3),
+                                 "model": "leaf flops / probe TF32 rate + addition bytes / HBM copy bandwidth"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_gflops()
+        cpu = cpu_oracle_headline(A_h, B_h, depth)
 
     value = flops * world / ms / 1e6
     line = {

@@ -280,11 +280,13 @@ fmm_status_t fmm_mlp_train_step(float* params, float* adam_m, float* adam_v, int
  * autotuner. */
 fmm_status_t fmm_set_cost_model(const float* params, const float* mean6, const float* std6);
 
-/* Allocation-free variant of fmm_gemm for callers that cannot allocate
- * device memory at call time -- code running inside CUDA stream capture
- * (where cudaMalloc is not permitted), allocator-less embedding contexts, or
- * hot paths whose memory budget is fixed up front.  The paper has no
- * counterpart; it is a deployment convenience.
+/* Allocation-free variant of fmm_gemm.  The paper has no counterpart; this is
+ * a deployment convenience for callers that cannot allocate device memory when
+ * they multiply: a host runtime whose device memory is reserved up front by
+ * another allocator (so a cudaMalloc would fail or break its accounting),
+ * embeddings that hand this library no allocator and no workspace, and
+ * latency-bound paths that must not pay for an allocation or a
+ * synchronising free.
  *
  * Computes C <- alpha * A * B + beta * C (row-major device pointers, the same
  * conventions as fmm_gemm) with one Winograd level over 3xTF32 tensor-core
@@ -292,14 +294,40 @@ fmm_status_t fmm_set_cost_model(const float* params, const float* mean6, const f
  * into the library (held by every GPU that loads it until the process exits),
  * so M, N and K must each be <= 1024; larger sizes return FMM_ERR_INVALID_ARG
  * with the limit in fmm_last_error().  The call allocates nothing (no
- * cudaMalloc/cudaFree, no host heap).  The first call on a device looks up the
- * array's device address (once per device, with that device current); make
- * that first call before any stream capture.  Every call clears the status
- * word it uses.  All calls share the one array, so calls that overlap on the
- * GPU (different streams, or different threads on the same device) race and
- * must be serialised by the caller. */
+ * cudaMalloc/cudaFree, no host heap, no allocating library routine).  The
+ * first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Every call clears the status word it uses, so fmm_gemm_static_status reports
+ * on the last call.  All calls share the one array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams, or
+ * different threads on the same device) race and must be serialised by the
+ * caller. */
 fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
                              const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                             fmm_stream_t stream);
+
+/* Device status of the last fmm_gemm_static call on the current device:
+ * synchronises `stream` (the stream of that call), reads the status word in
+ * the library's fixed array and clears it.  FMM_OK, FMM_ERR_TIMEOUT when one
+ * of the call's bounded device waits ran out (C is then incomplete), or
+ * FMM_ERR_CUDA for any other device-side error bit.  Allocates nothing. */
+fmm_status_t fmm_gemm_static_status(fmm_stream_t stream);
+
+/* Measurement helper, not part of the method: the tensor-pipe rate of this
+ * GPU, the ceiling the leaf launches are judged against.  Launches, on
+ * `stream`, one CTA pair per two SMs that issues tcgen05.mma back to back on
+ * operand tiles held in shared memory, in the leaf kernel's instruction shape
+ * (cta_group::2, M = 256, N = 256, K-major operands with 128-byte swizzle):
+ * kind = 0 kind::tf32 (K = 8 per instruction), kind = 1 kind::f16 on bf16
+ * operands (K = 16).  Each pair issues batches x 64 instructions, at most two
+ * batches queued.  fill: device buffer of at least 16384 floats (16-byte
+ * aligned) copied into every CTA's tiles (use random values: the tensor core's
+ * power draw, hence its clock under the power cap, depends on them).  One
+ * untimed launch, then one launch timed with CUDA events; synchronises.
+ * *tflops = 2 * 256 * 256 * K * 64 * batches * pairs / time; *ms (nullable) the
+ * timed launch.  Errors: INVALID_ARG (kind, batches outside 1 .. 2^24, NULL),
+ * ALIGNMENT, NO_DEVICE, CUDA, TIMEOUT (a bounded wait ran out). */
+fmm_status_t fmm_tensor_peak(int kind, int64_t batches, const float* fill, double* tflops, double* ms,
                              fmm_stream_t stream);
 
 /* Phase profiling.  fmm_plan_profile(plan, 1) resets the counters and makes

@@ -227,16 +227,6 @@ def winograd(A: np.ndarray, B: np.ndarray, depth: int, odd: str = "pad",
     raise ValueError(f"unknown odd-size mode {odd!r}")
 
 
-def winograd_gemm(alpha, A, B, beta, C, depth, odd="pad", dtype=np.float32):
-    """C <- alpha * W(A, B) + beta * C with the recursion evaluated in `dtype`,
-    the final scaling in float64 (beta = 0: C not read)."""
-    P = winograd(A.astype(dtype), B.astype(dtype), depth, odd).astype(np.float64)
-    out = float(alpha) * P
-    if beta != 0 and C is not None:
-        out = out + float(beta) * C.astype(np.float64)
-    return out
-
-
 # ---------------------------------------------------------------------------
 # Error measure and residual check
 # ---------------------------------------------------------------------------

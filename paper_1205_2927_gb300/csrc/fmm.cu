@@ -1883,7 +1883,26 @@ constexpr long long kStaticMaxDim = 1024;
 // status block + 7 child operands per side + 7 products, each (1024/2)^2 floats
 constexpr size_t kStaticBytes = 256 + 3 * (size_t)7 * (kStaticMaxDim / 2) * (kStaticMaxDim / 2) * sizeof(float);
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+// device address of the array, per device; filled on a device's first call and
+// read under g_mu, so host threads making first calls at once do not race
 void* g_static_scratch_addr[64] = {};
+
+// The array's device address on the current device (looked up once per device,
+// with that device current: the host-side name of the array is not a device
+// address).
+fmm_status_t static_scratch(void** out) {
+    int dev = 0;
+    FMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return FMM_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_static_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        FMM_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_static_scratch_addr[dev] = ptr;
+    }
+    *out = g_static_scratch_addr[dev];
+    return FMM_OK;
+}
 }  // namespace
 
 extern "C" fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
@@ -1903,17 +1922,12 @@ extern "C" fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float a
     DeviceInfo di;
     fmm_status_t s = device_info(&di);
     if (s != FMM_OK) return s;
-    int dev = 0;
-    FMM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return FMM_ERR_NO_DEVICE;
-    if (!g_static_scratch_addr[dev]) {
-        // once per device, with that device current: the host-side name of the
-        // array is not a device address
-        void* ptr = nullptr;
-        FMM_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
-        g_static_scratch_addr[dev] = ptr;
-    }
+    void* scratch = nullptr;
+    if ((s = static_scratch(&scratch)) != FMM_OK) return s;
     if (alpha == 0.0f || K == 0) {
+        // no kernel of this call can report into the status word: clear it so
+        // that fmm_gemm_static_status describes this call
+        FMM_CUDA(cudaMemsetAsync(scratch, 0, 64 * sizeof(unsigned), stream));
         FMM_CUDA(launch_scale(C, ldc, M, N, beta, stream));
         return FMM_OK;
     }
@@ -1931,11 +1945,26 @@ extern "C" fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float a
     size_t need = 0;
     layout(&p, nullptr, &need);
     if (need > kStaticBytes) return FMM_ERR_WORKSPACE;
-    p.ws = static_cast<char*>(g_static_scratch_addr[dev]);
+    p.ws = static_cast<char*>(scratch);
     p.ws_bytes = kStaticBytes;
     p.num_sms = di.num_sms;
     layout(&p, p.ws, nullptr);
     // the array keeps the previous call's contents: the status word must start at zero
     FMM_CUDA(cudaMemsetAsync(p.status, 0, 64 * sizeof(unsigned), stream));
     return execute(&p, alpha, A, B, beta, C, stream);
+}
+
+extern "C" fmm_status_t fmm_gemm_static_status(fmm_stream_t stream) {
+    DeviceInfo di;
+    fmm_status_t s = device_info(&di);
+    if (s != FMM_OK) return s;
+    void* scratch = nullptr;
+    if ((s = static_scratch(&scratch)) != FMM_OK) return s;
+    FMM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned w = 0;
+    // the status word is the first word of the array (the layout's first carve-out)
+    FMM_CUDA(cudaMemcpy(&w, scratch, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w) FMM_CUDA(cudaMemset(scratch, 0, sizeof(unsigned)));
+    if (w & FMM_DEV_TIMEOUT_BIT) return FMM_ERR_TIMEOUT;
+    return w ? FMM_ERR_CUDA : FMM_OK;
 }

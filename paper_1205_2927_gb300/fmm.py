@@ -86,6 +86,10 @@ def _load():
     lib.fmm_residual.restype = C.c_int
     lib.fmm_gemm_static.argtypes = [i64, i64, i64, C.c_float, vp, i64, vp, i64, C.c_float, vp, i64, vp]
     lib.fmm_gemm_static.restype = C.c_int
+    lib.fmm_gemm_static_status.argtypes = [vp]
+    lib.fmm_gemm_static_status.restype = C.c_int
+    lib.fmm_tensor_peak.argtypes = [C.c_int, i64, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    lib.fmm_tensor_peak.restype = C.c_int
     return lib
 
 
@@ -184,15 +188,56 @@ def fmm_residual(A, B, Cm, x, fp64=False, stream=None):
     return r
 
 
+def _check_static_operands(A, B, Cm):
+    """Shape, dtype, device and layout checks of fmm_gemm_static's tensors, made
+    before any call into the library: M, N, K are taken from A and B, so a short
+    B or a small C would otherwise be read or written past its end."""
+    import torch
+    for name, t in (("A", A), ("B", B), ("C", Cm)):
+        if t.dim() != 2:
+            raise ValueError(f"fmm_gemm_static: {name} must be a 2-D tensor")
+    M, K = A.shape
+    if B.shape[0] != K:
+        raise ValueError(f"fmm_gemm_static: B has {B.shape[0]} rows, A has {K} columns")
+    if tuple(Cm.shape) != (M, B.shape[1]):
+        raise ValueError(f"fmm_gemm_static: C is {tuple(Cm.shape)}, expected {(M, B.shape[1])}")
+    for name, t in (("A", A), ("B", B), ("C", Cm)):
+        if t.dtype != torch.float32:
+            raise TypeError(f"fmm_gemm_static: {name} must be float32, got {t.dtype}")
+        if not t.is_cuda:
+            raise ValueError(f"fmm_gemm_static: {name} must be a CUDA tensor")
+        if t.shape[0] > 0 and t.shape[1] > 1 and t.stride(1) != 1:
+            raise ValueError(f"fmm_gemm_static: {name} must have unit column stride")
+
+
 def fmm_gemm_static(A, B, Cm, alpha=1.0, beta=0.0, stream=None):
     """Cm <- alpha A B + beta Cm through the allocation-free entry point (device
-    tensors, row-major, unit column stride; M, N, K <= 1024)."""
+    float32 tensors, row-major, unit column stride; M, N, K <= 1024)."""
+    _check_static_operands(A, B, Cm)
     M, K = A.shape
     N = B.shape[1]
     _check(_lib.fmm_gemm_static(M, N, K, float(alpha), A.data_ptr(), max(A.stride(0), 1), B.data_ptr(),
                                 max(B.stride(0), 1), float(beta), Cm.data_ptr(), max(Cm.stride(0), 1),
                                 _stream_ptr(stream)), "fmm_gemm_static")
     return Cm
+
+
+def fmm_gemm_static_status(stream=None):
+    """Device status of the last fmm_gemm_static call (synchronises `stream`)."""
+    return _lib.fmm_gemm_static_status(_stream_ptr(stream))
+
+
+def fmm_tensor_peak(kind="tf32", batches=20000, seed=1, stream=None):
+    """Tensor-pipe rate of this GPU in TFLOP/s (measurement helper): back-to-back
+    tcgen05.mma of the leaf kernel's shape on shared-memory tiles filled with
+    uniform random values.  Returns (tflops, ms of the timed launch)."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    fill = (torch.rand(16384, generator=g) * 2 - 1).cuda()
+    tf, ms = C.c_double(), C.c_double()
+    _check(_lib.fmm_tensor_peak({"tf32": 0, "bf16": 1}[kind], int(batches), fill.data_ptr(), C.byref(tf),
+                                C.byref(ms), _stream_ptr(stream)), "fmm_tensor_peak")
+    return tf.value, ms.value
 
 
 def fmm_plan_phase_bytes(plan):

@@ -174,3 +174,33 @@ def test_classical_recursion_options(F):
     lib = F.library()
     o = F.options(algo="classical", host_operands=1)
     assert lib.fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 6
+
+
+def test_static_wrapper_rejects_bad_operands_before_any_call(F, monkeypatch):
+    torch = pytest.importorskip("torch")
+
+    class NoCall:
+        def __getattr__(self, name):
+            raise AssertionError(f"the library was called ({name}) before the operand checks")
+
+    monkeypatch.setattr(F, "_lib", NoCall())
+    A = torch.zeros(8, 6)
+    B = torch.zeros(6, 5)
+    cases = [
+        (A, torch.zeros(5, 5), torch.zeros(8, 5), ValueError, "rows"),       # B shorter than A's K
+        (A, B, torch.zeros(7, 5), ValueError, "expected"),                   # C too small
+        (A, B, torch.zeros(8, 4), ValueError, "expected"),
+        (A, B.reshape(-1), torch.zeros(8, 5), ValueError, "2-D"),
+        (A.double(), B, torch.zeros(8, 5), TypeError, "float32"),
+        (A, B, torch.zeros(8, 5), ValueError, "CUDA"),                       # host tensors
+    ]
+    for a, b, c, exc, text in cases:
+        with pytest.raises(exc, match=text):
+            F.fmm_gemm_static(a, b, c)
+
+
+def test_static_status_without_gpu_is_no_device(F):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    assert F.library().fmm_gemm_static_status(None) == 8

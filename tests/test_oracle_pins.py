@@ -366,3 +366,155 @@ def test_adam_step_matches_scalar_loop_and_decreases_loss():
         _, g = O.mlp_grad(th, X, t)
         th, mm, vv = O.adam_step(th, mm, vv, g, s, 3e-3)
     assert O.mlp_loss(th, X, t) < 0.5 * loss0
+
+
+# --- sampled rows ----------------------------------------------------------------
+
+def test_classical_rows_equals_full_rows_on_integers():
+    A = I.small_int((23, 17), 401, r=7)
+    B = I.small_int((17, 29), 402, r=7)
+    rows = [0, 22, 5, 5, 11, 1]          # any order, repeats allowed
+    full = brute_matmul(A.astype(np.int64).tolist(), B.astype(np.int64).tolist())
+    got = O.classical_rows(A, B, rows)
+    assert got.dtype == np.float64
+    assert got.tolist() == [[float(v) for v in full[r]] for r in rows]
+    # a transposed right operand (a plausible indexing mistake) does not pass
+    Bsq = I.small_int((17, 17), 403, r=7)
+    bad = np.matmul(A[rows].astype(np.float64), Bsq.T.astype(np.float64))
+    want = brute_matmul(A.astype(np.int64).tolist(), Bsq.astype(np.int64).tolist())
+    assert O.classical_rows(A, Bsq, rows).tolist() == [[float(v) for v in want[r]] for r in rows]
+    assert bad.tolist() != [[float(v) for v in want[r]] for r in rows]
+
+
+# --- IEEE half split ---------------------------------------------------------------
+
+_F = fractions.Fraction
+
+
+def _round_half_reference(v):
+    """Round a rational v to IEEE binary16 with ties to even, by exact rational
+    arithmetic: 10 fraction bits for |v| >= 2^-14, the fixed subnormal quantum
+    2^-24 below it, +-inf past the largest finite value 65504."""
+    if v == 0:
+        return 0.0
+    a = abs(v)
+    e = math.floor(math.log2(a))
+    while _F(2) ** e > a:          # exact floor(log2(a)) for a rational
+        e -= 1
+    while _F(2) ** (e + 1) <= a:
+        e += 1
+    q = _F(2) ** (max(e, -14) - 10)
+    f = math.floor(a / q)
+    r = a / q - f
+    if r > _F(1, 2) or (r == _F(1, 2) and f % 2 == 1):
+        f += 1
+    out = f * q
+    if out > 65504:
+        return math.copysign(math.inf, v)
+    return math.copysign(float(out), v)
+
+
+def _split_half_reference(x, scale):
+    xs = _F(float(np.float32(x))) * _F(scale)          # the scale is a power of two: exact
+    hi = _round_half_reference(xs)
+    lo = _round_half_reference(xs - _F(hi))              # x*s - hi is exact in fp32 and here
+    return hi, lo
+
+
+def _fp16_cases(scale=1.0):
+    """Normals, subnormals, ties and the largest finite half, kept within range
+    after scaling (the split's precondition)."""
+    tiny = np.array([2.0 ** -24, 3 * 2.0 ** -25, 2.0 ** -25, 2.0 ** -26, 2.0 ** -14 - 2.0 ** -24,
+                     2.0 ** -14, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -11 + 2.0 ** -20,
+                     2047.5, 2048.5, 65504.0, -(1.0 + 2.0 ** -11), 0.0], dtype=np.float32)
+    xs = np.concatenate([tiny, -tiny, I.normal((300,), 404), I.log_uniform((300,), 405),
+                           I.log_uniform((200,), 406, -7.5, -4.0)]).astype(np.float32)
+    return xs[np.abs(xs.astype(np.float64)) * scale <= 65504.0]
+
+
+@pytest.mark.parametrize("scale", [1.0, 2.0 ** 5, 2.0 ** -3])
+def test_split_fp16_matches_exact_rounding(scale):
+    xs = _fp16_cases(scale)
+    hi, lo = O.split_fp16(xs, scale)
+    for x, h, l in zip(xs.tolist(), hi.tolist(), lo.tolist()):
+        rh, rl = _split_half_reference(x, scale)
+        assert (h, l) == (rh, rl), (x, scale, h, l, rh, rl)
+
+
+def test_split_fp16_planted_mistakes_are_caught():
+    xs = _fp16_cases(2.0 ** 5)
+    ref = [_split_half_reference(x, 2.0 ** 5) for x in xs.tolist()]
+
+    def truncating(x, scale):            # round toward zero instead of to nearest
+        v = np.asarray(x, np.float32) * np.float32(scale)
+        hi = np.array([math.copysign(float(_F(abs(float(t))) // _F(2) ** (max(math.frexp(abs(t))[1] - 1, -14) - 10)
+                                           * _F(2) ** (max(math.frexp(abs(t))[1] - 1, -14) - 10)), t)
+                       if t != 0 else 0.0 for t in v.tolist()], dtype=np.float32)
+        lo = (v - hi).astype(np.float16).astype(np.float32)
+        return hi, lo
+
+    def double_scale(x, scale):          # the scale applied twice
+        return O.split_fp16(np.asarray(x, np.float32) * np.float32(scale), scale)
+
+    for bad in (truncating, double_scale):
+        with np.errstate(over="ignore"):      # the doubled scale overflows half on purpose
+            hi, lo = bad(xs, 2.0 ** 5)
+        assert [(h, l) for h, l in zip(hi.tolist(), lo.tolist())] != ref
+
+
+# --- cost-model network forward ------------------------------------------------------
+
+def _hand_network():
+    """A network whose output has a closed form: W1 copies the six features into
+    hidden units 0..5 (the rest get bias -1), W2 mixes three of them with an
+    asymmetric matrix (the rest get bias -1), W3 weighs the results."""
+    p = {name: np.zeros(shape) for name, shape in O.MLP_SHAPES}
+    for h in range(6):
+        p["W1"][h, h] = 1.0
+    p["b1"][6:] = -1.0
+    p["W2"][0, 1] = 2.0; p["b2"][0] = -1.0               # z2_0 = 2 h1 - 1
+    p["W2"][1, 0] = 1.0; p["W2"][1, 2] = -0.5            # z2_1 = h0 - 0.5 h2
+    p["W2"][2, 3] = 3.0; p["b2"][2] = 0.25               # z2_2 = 3 h3 + 0.25
+    p["b2"][3:] = -1.0
+    p["W3"][0, 0], p["W3"][0, 1], p["W3"][0, 2] = 1.0, -2.0, 0.5
+    p["W3"][0, 3:] = 0.1
+    p["b3"][0] = 0.3
+    return np.concatenate([p[name].reshape(-1) for name, _ in O.MLP_SHAPES])
+
+
+def _hand_output(x):
+    r = lambda v: max(v, 0.0)
+    h = [r(v) for v in x]
+    return r(2 * h[1] - 1) - 2 * r(h[0] - 0.5 * h[2]) + 0.5 * r(3 * h[3] + 0.25) + 0.3
+
+
+def _hand_inputs():
+    return np.array([[0.0] * 6, [1.0, 2.0, 0.5, -1.0, 3.0, -2.0], [-1.0, -2.0, -3.0, 0.5, 0.0, 1.0],
+                     [2.0, 0.25, 3.0, 1.0, -1.0, 0.0], [0.7, 0.6, -0.4, -0.1, 5.0, 5.0]])
+
+
+def test_mlp_forward_closed_form():
+    theta = _hand_network()
+    X = _hand_inputs()
+    y, _ = O.mlp_forward(theta, X)
+    assert y.tolist() == pytest.approx([_hand_output(x) for x in X.tolist()], abs=1e-15)
+
+
+def test_mlp_forward_planted_mistakes_are_caught():
+    theta = _hand_network()
+    X = _hand_inputs()
+    want = np.array([_hand_output(x) for x in X.tolist()])
+    p = O.mlp_unpack(theta)
+
+    def no_second_relu(X):
+        h1 = np.maximum(X @ p["W1"].T + p["b1"], 0.0)
+        h2 = h1 @ p["W2"].T + p["b2"]
+        return (h2 @ p["W3"].T + p["b3"])[:, 0]
+
+    def w2_transposed(X):
+        h1 = np.maximum(X @ p["W1"].T + p["b1"], 0.0)
+        h2 = np.maximum(h1 @ p["W2"] + p["b2"], 0.0)
+        return (h2 @ p["W3"].T + p["b3"])[:, 0]
+
+    for bad in (no_second_relu, w2_transposed):
+        assert np.max(np.abs(bad(X) - want)) > 0.1

@@ -1,10 +1,13 @@
 """The allocation-free entry point fmm_gemm_static, checked against the regular
 planned path (fmm_plan + fmm_gemm) on two calls in a row.
 
-fmm_gemm_static serves callers that cannot allocate device memory at call time
-(for example code inside CUDA stream capture, where cudaMalloc is not allowed):
-its temporaries live in a fixed device array compiled into the library, so M,
-N and K are limited to 1024.  This file is collected last on purpose."""
+fmm_gemm_static serves callers that cannot allocate device memory when they
+multiply: a runtime whose device memory another allocator reserved up front,
+an embedding that gives this library no allocator or workspace, a path that
+must not pay for an allocation.  Its temporaries live in a fixed device array
+compiled into the library, so M, N and K are limited to 1024.  This file is
+collected last on purpose, so that a run stopping at its first failure has run
+every other test before it."""
 import ctypes
 
 import numpy as np
@@ -41,6 +44,7 @@ def test_static_entry_matches_planned_path_twice():
         c_plan = torch.from_numpy(C0).cuda()
         st = f(m, n, k, 0.75, dA.data_ptr(), k, dB.data_ptr(), n, 0.5, c_static.data_ptr(), n, stream)
         assert st == 0, F.library().fmm_last_error()
+        assert F.fmm_gemm_static_status() == 0
         p = F.Plan(m, n, k, depth=1)
         p(dA, dB, c_plan, alpha=0.75, beta=0.5)
         torch.cuda.synchronize()
@@ -50,6 +54,44 @@ def test_static_entry_matches_planned_path_twice():
         ref = O.gemm(0.75, A, B, 0.5, C0)
         assert np.max(np.abs(got - ref)) / den <= BOUND
         p.close()
+
+
+def test_static_entry_allocates_no_device_memory():
+    # After one warm call (the first call on a device looks up the array's
+    # address), further calls leave the device's free memory unchanged.
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    m, k, n = 768, 1000, 640
+    A, B = I.operands(m, k, n, 12200)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    outs = [torch.empty(m, n, device="cuda") for _ in range(3)]
+    F.fmm_gemm_static(dA, dB, outs[0])
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    F.fmm_gemm_static(dA, dB, outs[1])
+    F.fmm_gemm_static(dA, dB, outs[2], alpha=-2.0)
+    assert F.fmm_gemm_static_status() == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    den = np.abs(A).max() * np.abs(B).max() * k
+    ref = O.classical(A, B)
+    assert np.max(np.abs(outs[1].cpu().numpy() - ref)) / den <= BOUND
+    assert np.max(np.abs(outs[2].cpu().numpy() + 2.0 * ref)) / (2.0 * den) <= BOUND
+
+
+def test_static_entry_alpha_zero_scales_c():
+    # alpha == 0 reads neither A nor B (NaN there must not show) and sets C <- beta C
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    m, k, n = 300, 200, 260
+    C0 = I.uniform((m, n), 12300)
+    dA = torch.full((m, k), float("nan"), device="cuda")
+    dB = torch.full((k, n), float("nan"), device="cuda")
+    dC = torch.from_numpy(C0).cuda()
+    F.fmm_gemm_static(dA, dB, dC, alpha=0.0, beta=0.5)
+    assert F.fmm_gemm_static_status() == 0
+    assert np.array_equal(dC.cpu().numpy(), (0.5 * C0).astype(np.float32))
 
 
 def test_static_entry_rejects_sizes_beyond_limit():
