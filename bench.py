@@ -648,6 +648,7 @@ def main():
     wplan = fmm.Plan(n, n, n, depth=args.depth, precision=args.precision, leaf_tile=args.leaf_tile)
     depth = wplan.info["depth"]
     bn = wplan.info["leaf_tile"]
+    fused_last = wplan.info["fuse_last"]
     step = lambda: wplan(dA, dB, dC)
 
     clocks = Clocks(local)
@@ -748,6 +749,8 @@ def main():
     traffic = ncu_traffic(os.path.join(ROOT, "paper_1205_2927_gb300", "csrc", "leaf_gemm.cu"),
                           f"n{n}_d{depth}_bn{bn}_{args.precision}")
     kname = "leaf_gemm_pair_kernel (cta_group::2, 256x256 tiles)" if bn == 512 else f"leaf_gemm_kernel (128x{bn} tiles)"
+    if fused_last:
+        kname += ", last Winograd level fused (node outputs, not products)"
     roofline = {"bound": "tensor", "kernel": kname + (" tcgen05 kind::tf32, pre-split raw/lo planes" if args.precision == "fp32"
                                                       else f" {args.precision}"),
                 "achieved": round(achieved, 1), "peak": round(peak_tc, 1), "unit": "TFLOP/s",
@@ -797,6 +800,7 @@ def main():
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"winograd_{args.precision}_square_n{n}", "n": n, "depth": depth, "leaf_tile": bn,
+                   "fuse_last": int(fused_last),
                    "precision": "fp32 via 3xTF32 tensor-core leaves" if args.precision == "fp32" else args.precision,
                    "dist": "A,B ~ U[-1,1] seeded", "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": f"replicas{world}"},

@@ -101,6 +101,13 @@ typedef struct {
     fmm_algo_t algo;
     int host_operands;         /* 1: A, B, C may be pinned host memory (streamed in/out) */
     int refine_fp64;           /* reserved: residual refinement in float64 (fmm_residual) */
+    int fuse_last;             /* last Winograd level inside the leaf launch: the seven products
+                                  of each last-level node are folded into the node's output
+                                  quadrants as they complete (the U-chain in its own order, so
+                                  the result is bitwise that of the separate post-addition
+                                  pass) and never stored.  Applies to depth-2 and depth-3 plans
+                                  on CTA-pair tiles with split-plane leaves (FP32, BF16X3,
+                                  FP16X3; device operands).  1 on, -1 off, 0 library default */
 } fmm_options_t;
 
 typedef struct fmm_plan_s* fmm_plan_t;
@@ -211,6 +218,11 @@ fmm_status_t fmm_wait_selftest(fmm_plan_t plan, int64_t limit_ns, fmm_stream_t s
  * uses (after the planner ran); any pointer may be NULL. */
 fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* precision,
                            int* odd, int* algo);
+
+/* Whether the plan's leaf launches fold the last Winograd level into the node
+ * outputs (fmm_options_t.fuse_last after the planner ran; for host-resident
+ * plans, their device-resident child plan): *fused = 1 or 0. */
+fmm_status_t fmm_plan_fuse_last(fmm_plan_t plan, int* fused);
 
 /* Freivalds residual of a computed product: r = C x - A (B x) for a probe
  * vector x (N entries, device; +-1 entries make a single wrong C entry show up

@@ -172,6 +172,11 @@ struct fmm_plan_s {
     int pair = 0;        // leaves on CTA pairs (cta_group::2), 256 x 256 tiles
     int tile_req = 256;  // leaf tile the plan was made for (512: CTA pairs where the precision allows)
     int rmul = 0;        // classical recursion (Table 1) depth; the Winograd depth is then 0
+    // the last Winograd level inside the leaf launch (CTA pairs, split planes,
+    // depth 2 or 3): the launch writes the level-(d-1) node outputs, not the
+    // 7^d products, through per-pair running tiles (fuse_scratch)
+    int fused = 0;
+    float* fuse_scratch = nullptr;
     char* tile_sched = nullptr;   // dynamic tile order of the leaf launches (counter + rings)
     int sched = 1;                // 0: static tile order, no scheduling area (the allocation-free entry)
     void* a16[2] = {};   // hi, lo planes of the leaf A operands (stack or the whole A)
@@ -325,14 +330,20 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
             L.bchild = cv.take<float>((size_t)(L.nodes * per * C.n * C.k));
         }
         const Level& Lf = p->lv[d];
-        p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
+        if (!p->fused) p->P = cv.take<float>((size_t)(Lf.nodes * Lf.m * Lf.n));
         for (int l = 1; l < d; ++l) {
+            if (p->fused && l == d - 1) {   // written by the leaf launch itself
+                Level& L = p->lv[l];
+                L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
+                continue;
+            }
             if (p->fuse_post() && (l == d - 1 || l == d - 2)) continue;   // fused away
             if (p->fuse_root_post() && l == d - 1) continue;
             if (p->fuse_root_post3()) continue;
             Level& L = p->lv[l];
             L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
         }
+        if (p->fused) p->fuse_scratch = cv.take<float>(kFuseMaxPairs * kFuseBytesPerPair / sizeof(float));
         if (p->peel && (p->Mw < p->M || p->Kw < p->K || p->Nw < p->N)) {
             // border products (classical leaves) read B transposed and A TMA-aligned
             p->ld_bt = rup(p->K, 4);
@@ -372,6 +383,7 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
     if (o->algo == FMM_ALGO_CLASSICAL && o->host_operands) return FMM_ERR_UNSUPPORTED;
     if (o->host_operands && o->odd != FMM_ODD_PAD) return FMM_ERR_UNSUPPORTED;
+    if (o->fuse_last < -1 || o->fuse_last > 1) return FMM_ERR_INVALID_ARG;
     return FMM_OK;
 }
 
@@ -383,6 +395,10 @@ int leaf_mode(fmm_precision_t p) {
         default: return kLeaf3xTF32;
     }
 }
+
+// Whether plans that can fuse the last Winograd level into the leaf launch do
+// so when the caller leaves fmm_options_t.fuse_last at 0.
+constexpr bool kFuseLastDefault = true;
 
 // Fixed-threshold planner: one more level while every dimension of the next
 // level's leaves stays at or above the cut-off (the recursion point of Sec. 3.1).
@@ -445,6 +461,7 @@ fmm_status_t run_leaves(fmm_plan_s* p, GemmArgs& args, cudaStream_t stream, int 
             args.tile_counter = reinterpret_cast<int*>(p->tile_sched);
             args.tile_seq = reinterpret_cast<unsigned long long*>(p->tile_sched + 256);
         }
+        args.fuse_scratch = p->fused ? p->fuse_scratch : nullptr;
         FMM_CUDA(launch_leaf_gemm_pair(args, mode, p->num_sms, stream));
         p->launches += args.total_tiles > 0 ? 1 : 0;
         return FMM_OK;
@@ -732,6 +749,12 @@ fmm_status_t winograd_leaf_groups(fmm_plan_s* p, CUtensorMap* maps, int& nm, Gem
         memset(&G, 0, sizeof(G));
         G.M = (int)mm; G.N = (int)nn; G.K = (int)kk; G.batch = (int)batch;
         G.C = p->P; G.ldc = nn; G.c_batch_stride = mm * nn;
+        if (p->fused) {
+            // schedule units are (last-level node, tile); the launch writes the
+            // node outputs (2 mm x 2 nn each, quadrants of the U-chain)
+            G.batch = (int)Ll.nodes;
+            G.C = Ll.cnode; G.ldc = Ll.n; G.c_batch_stride = Ll.m * Ll.n;
+        }
         G.alpha = 1.f; G.beta = 0.f; G.map_a = nm; G.map_a_lo = nm + 1; G.map_b = nm + 2; G.map_b_lo = nm + 3;
         G.vec_ok = 1;
         nm += 4;
@@ -795,6 +818,20 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
     Level* lv = p->lv;
     int top = d - 1;
     const double root_out = 4.0 * (double)(p->Mw * p->Nw) * (beta != 0.0f ? 2.0 : 1.0);
+    if (p->fused) {
+        // the leaf launch left the level-(d-1) node outputs: the remaining levels
+        // straight into the caller's C
+        const Level& L = lv[d - 1];
+        if (d == 3)
+            FMM_CUDA(launch_post_add2(L.cnode, L.n, L.m * L.n, 1, L.m, L.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
+                                      stream));
+        else
+            FMM_CUDA(launch_post_add(L.cnode, L.n, L.m * L.n, 1, L.m, L.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
+                                     stream));
+        p->launches += 1;
+        p->acct[1] += (double)L.nodes * 4.0 * (double)(L.m * L.n) + root_out;
+        return FMM_OK;
+    }
     if (p->fuse_root_post3()) {
         // all three levels at once: leaf products -> the caller's C
         const Level& Lf = lv[3];
@@ -1171,6 +1208,10 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
                  : o.precision == FMM_PREC_FP16X3 ? kLeafFP16x3P
                                                   : kLeaf3xTF32P;
     }
+    // the fused last level needs the CTA-pair kernel on split planes and a
+    // Winograd depth of 2 or 3 (the node outputs then fold into C in one pass)
+    const bool fusable = t.pair && t.pre16 && !t.host && t.rmul == 0 && (t.depth == 2 || t.depth == 3);
+    t.fused = fusable && (o.fuse_last > 0 || (o.fuse_last == 0 && kFuseLastDefault)) ? 1 : 0;
 }
 
 size_t plan_bytes(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,
@@ -1662,6 +1703,7 @@ fmm_status_t fmm_options_default(fmm_options_t* o) {
     o->algo = FMM_ALGO_WINOGRAD;
     o->host_operands = 0;
     o->refine_fp64 = 0;
+    o->fuse_last = 0;
     return FMM_OK;
 }
 
@@ -1857,6 +1899,12 @@ fmm_status_t fmm_wait_selftest(fmm_plan_t p, int64_t limit_ns, fmm_stream_t stre
     cudaStream_t stream = (cudaStream_t)stream_;
     p->last_stream = stream;
     FMM_CUDA(launch_wait_selftest(p->status, (unsigned long long)limit_ns, stream));
+    return FMM_OK;
+}
+
+fmm_status_t fmm_plan_fuse_last(fmm_plan_t p, int* fused) {
+    if (!p || !fused) return FMM_ERR_INVALID_ARG;
+    *fused = p->fused || (p->child && p->child->fused) ? 1 : 0;
     return FMM_OK;
 }
 

@@ -49,7 +49,12 @@ struct GemmArgs {
     // zero before the launch)
     int* tile_counter;
     unsigned long long* tile_seq;
+    // fused last Winograd level (CTA-pair launches): per-CTA running tiles, two
+    // of 128 x 256 floats per CTA (kFuseBytesPerPair per pair), or null
+    float* fuse_scratch;
 };
+constexpr int kFuseMaxPairs = 128;    // pairs a fused launch may use
+constexpr size_t kFuseBytesPerPair = 2 * 2 * 128 * 256 * sizeof(float);
 constexpr int kPairSeqSlots = 64;     // ring slots per CTA / pair (its roles stay within ~10 tiles)
 constexpr int kMaxSeqRings = 256;     // CTAs / pairs a dynamically scheduled launch may use
 constexpr size_t kTileSchedBytes = 256 + (size_t)kMaxSeqRings * kPairSeqSlots * 8;   // counter, then the rings

@@ -489,6 +489,60 @@ __global__ void __launch_bounds__(LeafCfg<BN, MODE>::kThreads, 1) leaf_gemm_kern
 //                         arrives once on CTA 0's accumulator-free barrier
 //   CTA 0      warp 1: MMA issuer; commits are multicast to both CTAs, so each
 //              CTA's producer waits on its own empty barrier
+//
+// FUSED: the last Winograd level inside the leaf launch.  A schedule unit is one
+// 256 x 256 tile position of one last-level node; the pair computes the node's
+// seven products at that position back to back, in the order P1, P2, P6, P7,
+// P5, P3, P4 (each into the next of the two accumulators), and the epilogue
+// folds each product into the node's four output quadrants as it lands:
+//   P1: X = P1            P2: C11 = X + P2      P6: X = X + P6 (U2)
+//   P7: Y = X + P7 (U3)   P5: X = X + P5 (U4), C22 = Y + P5 (U7)
+//   P3: C12 = X + P3 (U5) P4: C21 = Y - P4 (U6)
+// X and Y are per-CTA running tiles in a global scratch area (read back by the
+// same thread that wrote them; stored and loaded with an L2 evict-last policy so
+// that they stay on chip while the operand stream passes through L2).  These
+// are the fp32 additions of the U-chain in its own order, so the node outputs
+// equal those of storing the seven products and running the post-addition pass
+// over them, bit for bit; the products themselves never reach memory.
+// Leaf index of a unit's pp-th product: node * 7 + kFusedOrder[pp].
+__device__ __constant__ int kFusedOrder[7] = {0, 1, 5, 6, 4, 2, 3};
+
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float4* a, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float4 ld_keep(const float4* a, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(a), "l"(pol)
+                 : "memory");
+    return v;
+}
+
+// One 32-column chunk of a node-output quadrant (rows and columns of the leaf
+// tile; `o` already points at the quadrant's row) from 32 values in v.
+__device__ __forceinline__ void store_quadrant_chunk(float* o, const float (&v)[32], bool row_ok, int col0, int ncols,
+                                                     int vec_ok) {
+    if (!row_ok || col0 >= ncols) return;
+    if (vec_ok && col0 + 32 <= ncols) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+            __stcs(reinterpret_cast<float4*>(o + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+    } else {
+        const int lim = min(32, ncols - col0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < lim) o[j] = v[j];
+    }
+}
+
 template <int MODE>
 struct PairCfg {
     static constexpr bool kPlain = MODE == kLeafTF32;          // fp32 A | B tiles, one product
@@ -506,10 +560,11 @@ struct PairCfg {
     static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
-template <int MODE>
+template <int MODE, bool FUSED>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     leaf_gemm_pair_kernel(const __grid_constant__ GemmArgs args) {
     using Cfg = PairCfg<MODE>;
+    constexpr int kProducts = FUSED ? 7 : 1;   // products per schedule unit
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t base = (raw_addr + 1023u) & ~1023u;
@@ -588,7 +643,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 // column under the dynamic tile order, as in the MMA issuer)
                 const int ncols = dyn ? (int)tile_cols(G.N, tn, 256) : 256;
                 const int a0 = tm * 256 + (int)rank * Cfg::kRows, b0 = tn * 256 + (int)rank * (ncols / 2);
-                const int ab = b + G.a_batch_off, bb = b + G.b_batch_off;
+                for (int pp = 0; pp < kProducts && ok; ++pp) {
+                const int leaf = FUSED ? b * 7 + kFusedOrder[pp] : b;
+                const int ab = leaf + G.a_batch_off, bb = leaf + G.b_batch_off;
                 for (int kb = 0; kb < nk; ++kb) {
                     // the stage is free in this CTA once the MMAs that read it
                     // completed (their commit is multicast to both CTAs)
@@ -611,6 +668,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                     }
                     ++issued;
                     if (++stage == Cfg::kStages) { stage = 0; phase ^= 1u; }
+                }
                 }
             }
             // the copies of both CTAs complete on CTA 0's full barriers, and the
@@ -635,7 +693,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
                 const int nk = (groups[g].K + Cfg::kKB - 1) / Cfg::kKB;
                 const uint32_t idesc = idesc_with_n(idesc_full, dyn ? tile_cols(groups[g].N, tn, 256) : 256u);
-                if (!mbar_wait_cluster(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) break;
+                for (int pp = 0; pp < kProducts && ok; ++pp) {
+                if (!mbar_wait_cluster(tempty_bar(acc), acc_phase ^ 1u, abort_flag, status)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 256);
                 for (int kb = 0; kb < nk; ++kb) {
@@ -680,6 +739,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                 mma_commit_pair(tfull_bar(acc), (uint16_t)0x3);
                 acc ^= 1;
                 if (acc == 0) acc_phase ^= 1u;
+                }
             }
         }
     } else if (warp >= 4) {
@@ -687,7 +747,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         const int q = warp & 3;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (unsigned i = 0;; ++i) {
+        // FUSED: this CTA's running tiles X, Y (128 rows x 256 columns each),
+        // float4 (row r, columns c*32 + 4jj .. +3) at index (c * 8 + jj) * 128 + r,
+        // so a warp's accesses are 512 contiguous bytes
+        float4* X4 = nullptr;
+        uint64_t keep = 0;
+        if constexpr (FUSED) {
+            X4 = reinterpret_cast<float4*>(args.fuse_scratch) + (size_t)blockIdx.x * (2 * 128 * 256 / 4) + q * 32 + lane;
+            keep = l2_evict_last_policy();
+        }
+        bool stop = false;
+        for (unsigned i = 0; !stop; ++i) {
             long long t = pair + (long long)i * npairs;
             if (dyn) {
                 if (lane == 0) t = seq_read(seq + (i % kPairSeqSlots), i, abort_flag, status);
@@ -697,15 +767,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
             int g, b, tm, tn;
             decode_tile(groups, ng, args.raster_m, t, g, b, tm, tn);
             const GemmGroup& G = groups[g];
-            bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, status);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
             const int row = tm * 256 + (int)rank * Cfg::kRows + q * 32 + lane;
             const bool row_ok = row < G.M;
-            float* crow = G.C + (long long)b * G.c_batch_stride + (long long)(row_ok ? row : 0) * G.ldc;
             float alpha = G.alpha;
             const float beta = G.beta;
             if (MODE == kLeafFP16x3P && G.scale) alpha = alpha / (G.scale[0] * G.scale[1]);
+            for (int pp = 0; pp < kProducts; ++pp) {
+            bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, status);
+            if (!__all_sync(0xffffffffu, ok)) { stop = true; break; }
+            tc_fence_after();
+            if constexpr (!FUSED) {
+            float* crow = G.C + (long long)b * G.c_batch_stride + (long long)(row_ok ? row : 0) * G.ldc;
 #pragma unroll 1
             for (int c = 0; c < 256 / 32; ++c) {
                 uint32_t r[32];
@@ -743,6 +815,75 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
                     }
                 }
             }
+            } else {
+            // node output: quadrant (qi, qj) at rows qi * M + row, columns qj * N + col
+            float* node = G.C + (long long)b * G.c_batch_stride + (long long)(row_ok ? row : 0) * G.ldc;
+            const long long qrow = (long long)G.M * G.ldc;
+#pragma unroll 1
+            for (int c = 0; c < 256 / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256 + c * 32), r);
+                tmem_ld_wait();
+                const int col0 = tn * 256 + c * 32;
+                float4* xs = X4 + c * 8 * 128;
+                float4* ys = xs + 128 * 256 / 4;
+                float v[32], o[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = alpha * __uint_as_float(r[j]);
+                if (pp == 0) {                                      // P1: X = P1
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj)
+                        st_keep(xs + jj * 128, make_float4(v[4 * jj], v[4 * jj + 1], v[4 * jj + 2], v[4 * jj + 3]), keep);
+                } else if (pp == 2 || pp == 3) {                    // P6: X = X + P6;  P7: Y = X + P7
+                    float4 x[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) x[jj] = ld_keep(xs + jj * 128, keep);
+                    float4* dst = pp == 2 ? xs : ys;
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj)
+                        st_keep(dst + jj * 128, make_float4(x[jj].x + v[4 * jj], x[jj].y + v[4 * jj + 1],
+                                                            x[jj].z + v[4 * jj + 2], x[jj].w + v[4 * jj + 3]), keep);
+                } else if (pp == 4) {                               // P5: X = X + P5 (U4), C22 = Y + P5 (U7)
+                    float4 x[8], y[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) { x[jj] = ld_keep(xs + jj * 128, keep); y[jj] = ld_keep(ys + jj * 128, keep); }
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        st_keep(xs + jj * 128, make_float4(x[jj].x + v[4 * jj], x[jj].y + v[4 * jj + 1],
+                                                           x[jj].z + v[4 * jj + 2], x[jj].w + v[4 * jj + 3]), keep);
+                        o[4 * jj] = y[jj].x + v[4 * jj];
+                        o[4 * jj + 1] = y[jj].y + v[4 * jj + 1];
+                        o[4 * jj + 2] = y[jj].z + v[4 * jj + 2];
+                        o[4 * jj + 3] = y[jj].w + v[4 * jj + 3];
+                    }
+                    store_quadrant_chunk(node + qrow + G.N + col0, o, row_ok, col0, G.N, G.vec_ok);
+                } else {                                            // P2 -> C11, P3 -> C12 (from X); P4 -> C21 (from Y)
+                    const float4* src = pp == 6 ? ys : xs;
+                    float4 x[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) x[jj] = ld_keep(src + jj * 128, keep);
+                    if (pp == 6) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            o[4 * jj] = x[jj].x - v[4 * jj];
+                            o[4 * jj + 1] = x[jj].y - v[4 * jj + 1];
+                            o[4 * jj + 2] = x[jj].z - v[4 * jj + 2];
+                            o[4 * jj + 3] = x[jj].w - v[4 * jj + 3];
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            o[4 * jj] = x[jj].x + v[4 * jj];
+                            o[4 * jj + 1] = x[jj].y + v[4 * jj + 1];
+                            o[4 * jj + 2] = x[jj].z + v[4 * jj + 2];
+                            o[4 * jj + 3] = x[jj].w + v[4 * jj + 3];
+                        }
+                    }
+                    float* dst = pp == 1 ? node : pp == 5 ? node + G.N : node + qrow;
+                    store_quadrant_chunk(dst + col0, o, row_ok, col0, G.N, G.vec_ok);
+                }
+            }
+            }
             // every lane's tensor-memory reads are complete (wait::ld above);
             // one arrival per warp releases the accumulator to CTA 0's MMAs
             tc_fence_before();
@@ -753,6 +894,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
             }
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
+            }
         }
     }
 
@@ -764,10 +906,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     }
 }
 
-template <int MODE>
+template <int MODE, bool FUSED>
 static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStream_t stream) {
     using Cfg = PairCfg<MODE>;
-    auto kern = leaf_gemm_pair_kernel<MODE>;
+    auto kern = leaf_gemm_pair_kernel<MODE, FUSED>;
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -802,6 +944,7 @@ static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStrea
     }
     long long cap = (dev >= 0 && dev < 64) ? max_clusters[dev] : num_sms / 2;
     if (args.tile_counter && cap > kMaxSeqRings) cap = kMaxSeqRings;   // one ring per pair
+    if (FUSED && cap > kFuseMaxPairs) cap = kFuseMaxPairs;           // one pair of running tiles per pair
     if (args.total_tiles <= 0) return cudaSuccess;
     const long long pairs = args.total_tiles < cap ? args.total_tiles : cap;
     kern<<<(unsigned)(2 * pairs), Cfg::kThreads, Cfg::kSmem, stream>>>(args);
@@ -809,11 +952,21 @@ static cudaError_t launch_pair_impl(const GemmArgs& args, int num_sms, cudaStrea
 }
 
 cudaError_t launch_leaf_gemm_pair(const GemmArgs& args, int mode, int num_sms, cudaStream_t stream) {
+    if (args.fuse_scratch) {
+        // the fused last level reads every group as Winograd nodes of seven leaves
+        if (args.ext_groups || args.num_groups != 1 || args.groups[0].beta != 0.0f) return cudaErrorInvalidValue;
+        switch (mode) {
+            case kLeaf3xTF32P: return launch_pair_impl<kLeaf3xTF32P, true>(args, num_sms, stream);
+            case kLeafBF16x3P: return launch_pair_impl<kLeafBF16x3P, true>(args, num_sms, stream);
+            case kLeafFP16x3P: return launch_pair_impl<kLeafFP16x3P, true>(args, num_sms, stream);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (mode) {
-        case kLeafTF32: return launch_pair_impl<kLeafTF32>(args, num_sms, stream);
-        case kLeaf3xTF32P: return launch_pair_impl<kLeaf3xTF32P>(args, num_sms, stream);
-        case kLeafBF16x3P: return launch_pair_impl<kLeafBF16x3P>(args, num_sms, stream);
-        case kLeafFP16x3P: return launch_pair_impl<kLeafFP16x3P>(args, num_sms, stream);
+        case kLeafTF32: return launch_pair_impl<kLeafTF32, false>(args, num_sms, stream);
+        case kLeaf3xTF32P: return launch_pair_impl<kLeaf3xTF32P, false>(args, num_sms, stream);
+        case kLeafBF16x3P: return launch_pair_impl<kLeafBF16x3P, false>(args, num_sms, stream);
+        case kLeafFP16x3P: return launch_pair_impl<kLeafFP16x3P, false>(args, num_sms, stream);
         default: return cudaErrorInvalidValue;
     }
 }

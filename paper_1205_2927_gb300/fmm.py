@@ -41,7 +41,7 @@ class FmmError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("depth", C.c_int), ("cutoff", C.c_int), ("leaf_tile", C.c_int), ("precision", C.c_int),
                 ("odd", C.c_int), ("planner", C.c_int), ("algo", C.c_int), ("host_operands", C.c_int),
-                ("refine_fp64", C.c_int)]
+                ("refine_fp64", C.c_int), ("fuse_last", C.c_int)]
 
 
 def _load():
@@ -73,6 +73,8 @@ def _load():
     lib.fmm_get_device_status.restype = C.c_int
     lib.fmm_plan_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 5
     lib.fmm_plan_info.restype = C.c_int
+    lib.fmm_plan_fuse_last.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fmm_plan_fuse_last.restype = C.c_int
     lib.fmm_plan_profile.argtypes = [vp, C.c_int]
     lib.fmm_plan_profile.restype = C.c_int
     lib.fmm_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -106,7 +108,7 @@ def _check(status, where):
 
 
 def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="pad", planner="fixed",
-            algo="winograd", host_operands=0, refine_fp64=0) -> Options:
+            algo="winograd", host_operands=0, refine_fp64=0, fuse_last=0) -> Options:
     o = Options()
     _check(_lib.fmm_options_default(C.byref(o)), "fmm_options_default")
     o.depth, o.cutoff, o.leaf_tile = depth, cutoff, leaf_tile
@@ -115,6 +117,7 @@ def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="pad", pla
     o.planner = PLANNERS[planner] if isinstance(planner, str) else int(planner)
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.host_operands, o.refine_fp64 = host_operands, refine_fp64
+    o.fuse_last = int(fuse_last)
     return o
 
 
@@ -158,6 +161,12 @@ def fmm_plan_info(plan):
     vals = [C.c_int() for _ in range(5)]
     _check(_lib.fmm_plan_info(plan, *[C.byref(v) for v in vals]), "fmm_plan_info")
     return dict(zip(("depth", "leaf_tile", "precision", "odd", "algo"), [v.value for v in vals]))
+
+
+def fmm_plan_fuse_last(plan):
+    f = C.c_int()
+    _check(_lib.fmm_plan_fuse_last(plan, C.byref(f)), "fmm_plan_fuse_last")
+    return bool(f.value)
 
 
 def fmm_plan_profile(plan, enable=True):
@@ -265,6 +274,7 @@ class Plan:
         self.handle, _ = fmm_plan(self.M, self.N, self.K, self.lda, self.ldb, self.ldc, self.opt,
                                   self.workspace.data_ptr(), self.workspace.numel(), stream)
         self.info = fmm_plan_info(self.handle)
+        self.info["fuse_last"] = fmm_plan_fuse_last(self.handle)
 
     def __call__(self, A, B, C=None, alpha=1.0, beta=0.0, stream=None):
         import torch

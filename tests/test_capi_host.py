@@ -78,7 +78,8 @@ def test_workspace_closed_forms(F, n, d, prec, es):
     # the split planes (hi and lo, both sides, every leaf) plus the leaf
     # products are the whole workspace, apart from the status word and the
     # tile-scheduling area (< 256 KB): no transposed copies or middle levels
-    need = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512)
+    # (the unfused last level: fuse_last = -1; the fused layout has its own test)
+    need = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512, fuse_last=-1)
     leaves, h = 7 ** d, n >> d
     planes = 2 * 2 * leaves * h * h * es
     products = leaves * h * h * 4 if d > 0 else 0
@@ -204,3 +205,28 @@ def test_static_status_without_gpu_is_no_device(F):
     if torch.cuda.is_available():
         pytest.skip("a CUDA device is present")
     assert F.library().fmm_gemm_static_status(None) == 8
+
+
+@pytest.mark.parametrize("n,d,prec,es", [(16384, 3, "fp32", 4), (8192, 2, "fp32", 4), (8192, 3, "fp16x3", 2)])
+def test_fused_workspace_closed_forms(F, n, d, prec, es):
+    # fuse_last = 1: the split planes, the level-(d-1) node outputs (7^(d-1)
+    # nodes of (2h)^2 floats, h the leaf size) and the running tiles of up to
+    # 128 CTA pairs (512 KB each) replace the 7^d leaf products
+    need = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512, fuse_last=1)
+    leaves, h = 7 ** d, n >> d
+    planes = 2 * 2 * leaves * h * h * es
+    nodes = 7 ** (d - 1) * (2 * h) ** 2 * 4
+    running = 128 * 2 * 2 * 128 * 256 * 4
+    assert 0 <= need - planes - nodes - running < 256 * 1024, need - planes - nodes - running
+    # options a fused plan cannot take fall back to the unfused schedule
+    assert _query(F, n, n, n, depth=1, precision=prec, leaf_tile=512, fuse_last=1) == \
+        _query(F, n, n, n, depth=1, precision=prec, leaf_tile=512, fuse_last=-1)
+    assert _query(F, n, n, n, depth=d, precision="tf32", leaf_tile=512, fuse_last=1) == \
+        _query(F, n, n, n, depth=d, precision="tf32", leaf_tile=512, fuse_last=-1)
+
+
+def test_fuse_last_option_validated(F):
+    need = C.c_size_t(0)
+    for bad in (2, -2):
+        o = F.options(fuse_last=bad)
+        assert F.library().fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 1

@@ -17,6 +17,11 @@ from paper_1205_2927_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 FP32_BOUND = 2e-6
+# split-precision bounds: the FP32 bound scaled by each split's per-term error
+# bound against 3xTF32's 2^-19 (BF16x3 3 * 2^-16 -> 4.8e-5; TF32, one product
+# on truncated operands, 2^-10 -> 1.0e-3; FP16x3's 3 * 2^-22 is below 3xTF32's,
+# so it is held to the FP32 bound)
+SPLIT_BOUND = {"fp32": FP32_BOUND, "fp16x3": FP32_BOUND, "bf16x3": 4.8e-5, "tf32": 1.0e-3}
 
 
 @pytest.fixture(scope="module")
@@ -70,13 +75,30 @@ def device_run(F, A, B, **kw):
 
 
 def test_square_16384_bench_configuration(F):
-    # the bench's default launch: fixed planner, default cut-off 2048 -> depth 3,
-    # CTA-pair leaves
+    # the bench's default launch (fixed planner, default cut-off 2048 -> depth 3,
+    # CTA-pair leaves, the library's default fuse_last) on the bench's own
+    # operands, compared element by element with the full float64 product of
+    # the definition (one host dgemm of 16384^3)
     n = 16384
     A, B = I.operands(n, n, n, I.seed_for(2, 0))
     C, info = device_run(F, A, B, precision="fp32")
     assert (info["depth"], info["leaf_tile"]) == (3, 512)
+    C64 = O.classical(A, B)
+    den = float(np.abs(A).max()) * float(np.abs(B).max()) * n
+    err = np.abs(C.astype(np.float64) - C64)
+    assert np.all(np.isfinite(C))
+    assert float(err.max()) / den <= FP32_BOUND, float(err.max()) / den
+    del C64, err
     check(A, B, C, sample_rows(n, 3, 1), FP32_BOUND, I.seed_for(2, 90))
+
+
+def test_square_16384_fused_and_unfused_last_level_agree(F):
+    # the two schedules of the last Winograd level run the same fp32 additions
+    n = 16384
+    A, B = I.operands(n, n, n, I.seed_for(2, 0))
+    fused, _ = device_run(F, A, B, depth=3, leaf_tile=512, fuse_last=1)
+    plain, _ = device_run(F, A, B, depth=3, leaf_tile=512, fuse_last=-1)
+    assert np.array_equal(fused, plain)
 
 
 @pytest.mark.parametrize("odd", ["pad", "peel"])
@@ -88,11 +110,12 @@ def test_odd_19000_depth_2(F, odd):
     check(A, B, C, sample_rows(n, 2, 2), FP32_BOUND, I.seed_for(2, 91))
 
 
-@pytest.mark.parametrize("prec,dist,d,bound", [("fp32", "loguniform", 2, FP32_BOUND),
-                                               ("fp16x3", "normal", 2, FP32_BOUND),
-                                               ("bf16x3", "loguniform", 3, 5e-5),
-                                               ("tf32", "normal", 0, 5e-5)])
-def test_rectangular_19000x12000x15000_split_precision(F, prec, dist, d, bound):
+@pytest.mark.parametrize("prec,dist,d", [("fp32", "loguniform", 2), ("fp16x3", "normal", 2),
+                                         ("bf16x3", "loguniform", 3), ("bf16x3", "normal", 2),
+                                         ("fp16x3", "loguniform", 3), ("tf32", "normal", 0),
+                                         ("tf32", "loguniform", 2)])
+def test_rectangular_19000x12000x15000_split_precision(F, prec, dist, d):
+    bound = SPLIT_BOUND[prec]
     m, k, n = 19000, 12000, 15000
     A, B = I.operands(m, k, n, I.seed_for(3, m % 89), dist)
     C, info = device_run(F, A, B, depth=d, precision=prec)
@@ -137,6 +160,24 @@ def test_batched_512_uneven(F, tile):
         worst = max(worst, err)
     assert worst <= FP32_BOUND, worst
     bp.close()
+
+
+def test_host_resident_16384_depth3_equals_device(F):
+    # the bench's e2e leg: pinned host operands at the bench's depth (3), its
+    # transfers inside the call, against the device-resident depth-3 plan
+    import torch
+    n = 16384
+    A, B = I.operands(n, n, n, I.seed_for(2, 0))
+    dev, info = device_run(F, A, B, depth=3)
+    assert info["depth"] == 3
+    hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    hC = torch.full((n, n), float("nan")).pin_memory()
+    p = F.Plan(n, n, n, depth=3, host_operands=1)
+    p(hA, hB, hC)
+    torch.cuda.current_stream().synchronize()
+    assert p.device_status() == 0
+    p.close()
+    assert np.array_equal(hC.numpy(), dev)
 
 
 def test_host_resident_16384_equals_device(F):
