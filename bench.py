@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     ap.add_argument("--model-out", default=None,
                     help="planner workload: write the trained cost model to this file")
+    ap.add_argument("--model-in", default=None,
+                    help="batched workload: a trained cost model (planner workload's --model-out) for the learned planner")
     return ap.parse_args()
 
 
@@ -430,58 +432,58 @@ def wl_split(args):
 
 def wl_batched(args):
     """512 independent products, M, K, N log-uniform in [128, 4096] (multiples of 4),
-    U[-1,1]; one persistent leaf launch per replay of a CUDA graph; the leaf tile and the
-    per-problem depth cut-off are tuned by timing the whole batch (`--precision` selects
-    the leaves: fp32 = 3xTF32, tf32, bf16x3, fp16x3)."""
+    U[-1,1]; one persistent leaf launch per replay of a CUDA graph.  The plan
+    comes from the library: the fixed rule, the exhaustive per-size-class tuner
+    (fmm_batched_plan with planner="exhaustive": whole-batch timings, one depth
+    per class, one leaf tile per launch) and, with --model-in, the learned
+    planner (`--precision` selects the leaves: fp32 = 3xTF32, tf32, bf16x3,
+    fp16x3)."""
     import numpy as np
     import torch
     from paper_1205_2927_gb300 import fmm, inputs
+    from paper_1205_2927_gb300 import planner as PL
     shapes = inputs.batched_shapes(512, inputs.seed_for(4, 0))
     flops = sum(2.0 * m * k * n for m, k, n in shapes)
     As = [torch.from_numpy(inputs.uniform((m, k), inputs.seed_for(4, 1) + 3 * i)).cuda() for i, (m, k, n) in enumerate(shapes)]
     Bs = [torch.from_numpy(inputs.uniform((k, n), inputs.seed_for(4, 2) + 3 * i)).cuda() for i, (m, k, n) in enumerate(shapes)]
     Cs = [torch.empty((m, n), device="cuda") for m, k, n in shapes]
-    best = None
-    t_tune0 = time.perf_counter()
-    for bn in (128, 256, 512):
-        for cutoff in (1024, 2048, 8192):
-            bp = fmm.BatchedPlan(As, Bs, Cs, leaf_tile=bn, cutoff=cutoff, precision=args.precision)
-            s = torch.cuda.Stream()
-            s.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(s):
-                bp.run(s)
-            torch.cuda.current_stream().wait_stream(s)
-            torch.cuda.synchronize()
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                bp.run(torch.cuda.current_stream())
-            ms = event_ms(torch, g.replay, 20, 3)
-            info = bp.info()
-            rec = {"workload": "batched512", "precision": args.precision, "leaf_tile": bn, "cutoff": cutoff,
-                   "graph_replay_ms": round(ms, 3),
-                   "gflops": round(flops / ms / 1e6, 1), "total_flops": flops,
-                   "recursing_problems": int(sum(1 for d in info["depths"] if d > 0)),
-                   "leaf_tiles": info["total_tiles"]}
-            emit(args, rec)
-            if best is None or ms < best[0]:
-                best = (ms, bn, cutoff, g, bp)
-            else:
-                del g
-                bp.close()
-    tune_s = time.perf_counter() - t_tune0
-    ms, bn, cutoff, g, bp = best
-    g.replay()
-    torch.cuda.synchronize()
-    errs = []
-    for i in range(0, 512, 37):
-        A_h, B_h = As[i].cpu().numpy(), Bs[i].cpu().numpy()
-        ref = A_h.astype(np.float64) @ B_h.astype(np.float64)
-        errs.append(float(np.max(np.abs(Cs[i].cpu().numpy() - ref))) /
-                    (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * A_h.shape[1]))
-    emit(args, {"workload": "batched512_best", "precision": args.precision, "leaf_tile": bn, "cutoff": cutoff,
-                "graph_replay_ms": round(ms, 3),
-                "gflops": round(flops / ms / 1e6, 1), "tuning_s": round(tune_s, 2), "max_error_sampled": max(errs),
-                "launches_per_replay": "1 batched copy + pre/post of recursing problems + 1 persistent leaf launch"})
+    planners = ["fixed", "exhaustive"]
+    if args.model_in:
+        PL.register(*PL.load(args.model_in))
+        planners.append("mlp")
+    for planner in planners:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bp = fmm.BatchedPlan(As, Bs, Cs, planner=planner, precision=args.precision)
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            bp.run(s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bp.run(torch.cuda.current_stream())
+        ms = event_ms(torch, g.replay, 20, 3)
+        info = bp.info()
+        errs = []
+        for i in range(0, 512, 37):
+            A_h, B_h = As[i].cpu().numpy(), Bs[i].cpu().numpy()
+            ref = A_h.astype(np.float64) @ B_h.astype(np.float64)
+            errs.append(float(np.max(np.abs(Cs[i].cpu().numpy() - ref))) /
+                        (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * A_h.shape[1]))
+        depth_hist = {d: int(sum(1 for x in info["depths"] if x == d)) for d in sorted(set(info["depths"]))}
+        emit(args, {"workload": "batched512", "precision": args.precision, "planner": planner,
+                    "leaf_tile": info["leaf_tile"], "size_classes": info["nclasses"], "depths": depth_hist,
+                    "graph_replay_ms": round(ms, 3), "gflops": round(flops / ms / 1e6, 1), "total_flops": flops,
+                    "plan_s": round(plan_s, 2), "leaf_tiles": info["total_tiles"],
+                    "max_error_sampled": max(errs)})
+        del g
+        bp.close()
+    if args.model_in:
+        fmm.fmm_set_cost_model(None)
 
 
 def wl_residual(args):

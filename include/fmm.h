@@ -146,8 +146,9 @@ fmm_status_t fmm_gemm(fmm_plan_t plan, float alpha, const float* A, const float*
 /* Many independent products C_i <- alpha_i A_i B_i + beta_i C_i of uneven
  * sizes in one persistent tensor-core launch.  All arrays have `count`
  * entries and live in host memory; the matrices are device pointers.  With
- * workspace == NULL only *workspace_needed is set.  The per-size-class plan
- * (depth, leaf tile) follows opt->planner.  Asynchronous. */
+ * workspace == NULL only *workspace_needed is set.  The plan (each size
+ * class's depth, the launch's leaf tile) follows opt->planner as in
+ * fmm_batched_plan.  Asynchronous unless the planner times candidates. */
 fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, const int64_t* K,
                               const float* const* A, const int64_t* lda,
                               const float* const* B, const int64_t* ldb,
@@ -158,9 +159,23 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
 
 /* Batched plan: the same products as fmm_gemm_batched, split so that the
  * launches can be captured in a CUDA graph and replayed.  fmm_batched_plan
- * picks each problem's depth (opt->depth, or the fixed planner per problem),
- * encodes every tensor map and leaf descriptor and copies the tables into the
- * workspace (synchronously); fmm_batched_run then only launches kernels: one
+ * picks the depths and the leaf tile, encodes every tensor map and leaf
+ * descriptor and copies the tables into the workspace (synchronously).
+ * Problems fall into size classes (smallest and largest dimension, each
+ * rounded to a power of two); the launch has one leaf tile (opt->leaf_tile,
+ * or chosen):
+ *   opt->depth >= 0 or FMM_PLANNER_FIXED: the fixed rule per problem, tile
+ *     512 (CTA pairs) for the split-plane precisions, 256 for TF32;
+ *   FMM_PLANNER_EXHAUSTIVE: per leaf tile, one pass of coordinate descent over
+ *     the classes, largest work first, timing each class's candidate depths as
+ *     whole-batch launches on scratch outputs in the workspace (the caller's
+ *     A and B are read, C is not touched; synchronises `stream`);
+ *   FMM_PLANNER_MLP: the registered cost model scores every problem at every
+ *     candidate (depth, tile) in one inference launch; each class takes the
+ *     depth of least predicted sum, the launch the tile of least predicted
+ *     total (without a model: EXHAUSTIVE).
+ * A problem's depth never exceeds 4 or leaves below 64 wide.
+ * fmm_batched_run then only launches kernels: one
  * batched transpose/copy launch, the pre-additions of the problems that
  * recurse, ONE persistent leaf launch over every leaf product of every problem
  * (longest tiles first), and the post-additions; FP16x3 first derives every
@@ -179,6 +194,10 @@ void fmm_batched_free(fmm_batched_t plan);
 /* depths: `count` ints (-1 for problems with no product to compute); any
  * pointer may be NULL.  launches: kernels launched by all runs so far. */
 fmm_status_t fmm_batched_info(fmm_batched_t plan, int* depths, int64_t* total_tiles, int64_t* launches);
+/* classes: `count` ints, each problem's size class index (0 .. *nclasses - 1,
+ * -1 for problems with no product); *leaf_tile: the launch's leaf tile (512 =
+ * CTA pairs).  Any pointer may be NULL. */
+fmm_status_t fmm_batched_classes(fmm_batched_t plan, int* classes, int* nclasses, int* leaf_tile);
 
 /* Release a plan (NULL-safe).  Never frees the caller's workspace. */
 void fmm_free(fmm_plan_t plan);

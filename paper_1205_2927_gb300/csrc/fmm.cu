@@ -948,6 +948,9 @@ struct fmm_batched_s {
     std::vector<float*> C;
     std::vector<long long> M, N, ldc;
     std::vector<float> alpha, beta;
+    std::vector<int> cls;              // size class of each problem (-1: no product)
+    int nclasses = 0;
+    int tile = 512;                    // leaf tile of the launch (512: CTA pairs)
     long long launches = 0;
     ~fmm_batched_s() {
         for (auto* q : subs) delete q;
@@ -956,10 +959,29 @@ struct fmm_batched_s {
 
 namespace {
 
+// Deepest level a batched problem may take: at most 4, leaves at least 64 wide.
+int batched_max_depth(long long M, long long N, long long K) {
+    const long long mn = std::min(std::min(M, N), K);
+    int d = 4;
+    while (d > 0 && (mn >> d) < 64) --d;
+    return d;
+}
+
+// Depth of problem i under the fixed rule (or the caller's depth), kept to leaves
+// at least 64 wide; -1 for problems with no product to compute.
+int batched_fixed_depth(long long M, long long N, long long K, float alpha, const fmm_options_t& o) {
+    if (M == 0 || N == 0 || K == 0 || alpha == 0.0f) return -1;
+    int d = o.depth >= 0 ? o.depth : fixed_depth(M, N, K, o.cutoff);
+    return std::min(d, batched_max_depth(M, N, K));
+}
+
+// depth_in: per-problem depths chosen by a planner (nullptr: the fixed rule);
+// tile_req: the launch's leaf tile (0: from the options).
 fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const int64_t* N, const int64_t* K,
                            const float* const* A, const int64_t* lda, const float* const* B, const int64_t* ldb,
                            float* const* C, const int64_t* ldc, const float* alpha, const float* beta,
-                           const fmm_options_t& o, char* ws, size_t* needed) {
+                           const fmm_options_t& o, char* ws, size_t* needed, const int* depth_in = nullptr,
+                           int tile_req = 0) {
     Carver cv(ws);
     b->status = cv.take<unsigned>(64);
     b->count = count;
@@ -969,8 +991,10 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     // leaf tile 512 (and the default 0): 256 x 256 tiles on CTA pairs for the
     // pre-split precisions (512 uneven products: 8.70 ms per replay against 9.10
     // on single CTAs); TF32 batched launches stay on single CTAs (128 x 256)
-    b->pair = ((o.leaf_tile == 512 || o.leaf_tile == 0) && b->pre) ? 1 : 0;
-    b->bn = (o.leaf_tile && o.leaf_tile != 512) ? o.leaf_tile : 256;
+    const int lt = tile_req ? tile_req : o.leaf_tile;
+    b->pair = ((lt == 512 || lt == 0) && b->pre) ? 1 : 0;
+    b->bn = (lt && lt != 512) ? lt : 256;
+    b->tile = b->pair ? 512 : b->bn;
     if (b->pre) {
         b->split_kind = o.precision == FMM_PREC_BF16X3 ? kSplitBF16 : b->fp16 ? kSplitFP16 : kSplitTF32;
         b->mode = o.precision == FMM_PREC_BF16X3 ? kLeafBF16x3P : b->fp16 ? kLeafFP16x3P : kLeaf3xTF32P;
@@ -983,9 +1007,8 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
     for (int i = 0; i < count; ++i) {
         if (M[i] == 0 || N[i] == 0) { b->depth[i] = -1; continue; }
         if (K[i] == 0 || alpha[i] == 0.0f) { b->depth[i] = -1; b->scale_only[i] = 1; continue; }
-        int d = o.depth >= 0 ? o.depth : fixed_depth(M[i], N[i], K[i], o.cutoff);
-        const long long mn = std::min(std::min((long long)M[i], (long long)N[i]), (long long)K[i]);
-        while (d > 0 && (mn >> d) < 64) --d;  // keep leaves at least 64 wide
+        int d = depth_in ? std::min(std::max(depth_in[i], 0), batched_max_depth(M[i], N[i], K[i]))
+                         : batched_fixed_depth(M[i], N[i], K[i], alpha[i], o);
         b->depth[i] = d;
         if (b->pre) { total_maps += 4; total_groups += 1; total_jobs += d == 0 ? 2 : 0; }
         else if (d == 0) { total_maps += 2; total_groups += 1; total_jobs += 2; }
@@ -1595,48 +1618,9 @@ fmm_status_t fmm_autotune(int64_t M, int64_t N, int64_t K, const fmm_options_t* 
 
 }  // extern "C"
 
-extern "C" {
+namespace {
 
-fmm_status_t fmm_batched_plan(fmm_batched_t* out, int count, const int64_t* M, const int64_t* N, const int64_t* K,
-                              const float* const* A, const int64_t* lda, const float* const* B, const int64_t* ldb,
-                              float* const* C, const int64_t* ldc, const float* alpha, const float* beta,
-                              const fmm_options_t* opt, void* workspace, size_t workspace_bytes,
-                              size_t* workspace_needed, fmm_stream_t stream) {
-    (void)stream;
-    if (out) *out = nullptr;
-    fmm_status_t s = batched_check(count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, opt);
-    if (s != FMM_OK) return s;
-    fmm_options_t o;
-    if (opt) o = *opt; else fmm_options_default(&o);
-    size_t need = 0;
-    {
-        fmm_batched_s tmp;
-        if ((s = batched_build(&tmp, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, o, nullptr, &need)) != FMM_OK)
-            return s;
-    }
-    if (workspace_needed) *workspace_needed = need;
-    if (!out) return FMM_OK;
-    DeviceInfo di;
-    if ((s = device_info(&di)) != FMM_OK) return s;
-    if (count > 0 && (!A || !B || !C)) return FMM_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < need) return FMM_ERR_WORKSPACE;
-    if (reinterpret_cast<uintptr_t>(workspace) & 255) return FMM_ERR_ALIGNMENT;
-    fmm_batched_s* b = new (std::nothrow) fmm_batched_s();
-    if (!b) return FMM_ERR_OOM;
-    b->num_sms = di.num_sms;
-    if ((s = batched_build(b, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, o, static_cast<char*>(workspace),
-                           nullptr)) != FMM_OK) {
-        delete b;
-        return s;
-    }
-    for (auto* q : b->subs) q->num_sms = di.num_sms;
-    *out = b;
-    return FMM_OK;
-}
-
-fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
-    if (!b) return FMM_ERR_INVALID_ARG;
-    cudaStream_t stream = (cudaStream_t)stream_;
+fmm_status_t batched_run(fmm_batched_s* b, cudaStream_t stream) {
     fmm_status_t s;
     if (b->fp16 && b->count > 0) {   // per-problem operand scales first: the splits and sub-plans apply them
         FMM_CUDA(cudaMemsetAsync(b->d_absmax, 0, 2 * sizeof(unsigned) * (size_t)b->count, stream));
@@ -1681,7 +1665,323 @@ fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
     return FMM_OK;
 }
 
+
+// Size class of a batched problem: its smallest and largest dimension, each
+// rounded to the nearest power of two (the smallest sets how deep the
+// recursion can go; the largest, how much work a level saves).
+int size_class(long long M, long long N, long long K) {
+    const long long mn = std::min(std::min(M, N), K), mx = std::max(std::max(M, N), K);
+    const int a = (int)std::lround(std::log2((double)std::max(mn, 1LL)));
+    const int c = (int)std::lround(std::log2((double)std::max(mx, 1LL)));
+    return a * 64 + c;
+}
+
+// Leaf tiles a batched planner chooses among (one per launch).
+std::vector<int> batched_tiles(const fmm_options_t& o) {
+    if (o.leaf_tile) return {o.leaf_tile};
+    if (o.precision == FMM_PREC_TF32) return {256, 128};
+    return {512, 256};
+}
+
+struct BatchedTuner {
+    int count;
+    const int64_t *M, *N, *K, *lda, *ldb;
+    const float* const* A;
+    const float* const* B;
+    const float* alpha;
+    fmm_options_t o;
+    char* region;                 // where trial plans are built
+    std::vector<float*> Cs;       // scratch outputs (M_i x N_i)
+    std::vector<int64_t> ldc;
+    std::vector<float> zeros;
+    int num_sms;
+    cudaStream_t stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+
+    // Whole-batch time of one configuration: built in `region`, one untimed
+    // run, then the best of two timed runs.
+    fmm_status_t time(const std::vector<int>& depth, int tile, float* ms) {
+        fmm_batched_s t;
+        t.num_sms = num_sms;
+        fmm_status_t s = batched_build(&t, count, M, N, K, A, lda, B, ldb, Cs.data(), ldc.data(), alpha,
+                                       zeros.data(), o, region, nullptr, depth.data(), tile);
+        if (s != FMM_OK) return s;
+        for (auto* q : t.subs) q->num_sms = num_sms;
+        if ((s = batched_run(&t, stream)) != FMM_OK) return s;
+        float best = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            FMM_CUDA(cudaEventRecord(e0, stream));
+            if ((s = batched_run(&t, stream)) != FMM_OK) return s;
+            FMM_CUDA(cudaEventRecord(e1, stream));
+            FMM_CUDA(cudaEventSynchronize(e1));
+            float x = 0.f;
+            FMM_CUDA(cudaEventElapsedTime(&x, e0, e1));
+            best = std::min(best, x);
+        }
+        unsigned w = 0;
+        FMM_CUDA(cudaMemcpy(&w, t.status, sizeof(w), cudaMemcpyDeviceToHost));
+        if (w & FMM_DEV_TIMEOUT_BIT) return FMM_ERR_TIMEOUT;
+        *ms = best;
+        return FMM_OK;
+    }
+};
+
+// Per-size-class plan of a batched launch.  depth[i] receives every problem's
+// depth (-1: no product) and *tile the launch's leaf tile.
+//   FIXED       the fixed rule per problem (or the caller's depth).
+//   EXHAUSTIVE  for each leaf tile candidate, one pass of coordinate descent
+//               over the size classes (largest work first): every candidate
+//               depth of the class is timed as a whole-batch launch on scratch
+//               outputs, the others held; a change is kept when it saves >= 1 %.
+//   MLP         the registered cost model predicts log(ms) of every problem at
+//               every candidate (depth, tile) in one inference launch; each
+//               class takes the depth of least predicted sum, the launch the
+//               tile of least predicted total (no model: EXHAUSTIVE).
+// Scratch (EXHAUSTIVE / MLP) follows `region_bytes` in the workspace.
+fmm_status_t batched_choose(int count, const int64_t* M, const int64_t* N, const int64_t* K, const float* const* A,
+                            const int64_t* lda, const float* const* B, const int64_t* ldb, const float* alpha,
+                            const fmm_options_t& o, char* ws, size_t region_bytes, int num_sms, cudaStream_t stream,
+                            std::vector<int>& depth, std::vector<int>& cls, int& nclasses, int& tile) {
+    depth.assign(count, -1);
+    cls.assign(count, -1);
+    std::vector<int> ids;
+    for (int i = 0; i < count; ++i) {
+        depth[i] = batched_fixed_depth(M[i], N[i], K[i], alpha[i], o);
+        if (depth[i] < 0) continue;
+        const int c = size_class(M[i], N[i], K[i]);
+        auto it = std::find(ids.begin(), ids.end(), c);
+        cls[i] = (int)(it - ids.begin());
+        if (it == ids.end()) ids.push_back(c);
+    }
+    nclasses = (int)ids.size();
+    const std::vector<int> tiles = batched_tiles(o);
+    tile = o.leaf_tile ? o.leaf_tile : tiles[0];
+    if (o.planner == FMM_PLANNER_FIXED || o.depth >= 0 || nclasses == 0) return FMM_OK;
+    // classes, largest work first; a class's candidate depths reach its deepest member's limit
+    std::vector<double> work(nclasses, 0.0);
+    std::vector<int> cmax(nclasses, 0);
+    for (int i = 0; i < count; ++i)
+        if (cls[i] >= 0) {
+            work[cls[i]] += 2.0 * (double)M[i] * (double)N[i] * (double)K[i];
+            cmax[cls[i]] = std::max(cmax[cls[i]], batched_max_depth(M[i], N[i], K[i]));
+        }
+    std::vector<int> order(nclasses);
+    for (int c = 0; c < nclasses; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    auto with_class_depth = [&](const std::vector<int>& base, int c, int d) {
+        std::vector<int> r = base;
+        for (int i = 0; i < count; ++i)
+            if (cls[i] == c) r[i] = std::min(d, batched_max_depth(M[i], N[i], K[i]));
+        return r;
+    };
+    char* scratch = ws + align_up(region_bytes, 256);
+    if (o.planner == FMM_PLANNER_MLP && g_model.set) {
+        // rows: (problem, tile, depth) for every depth up to the problem's limit
+        std::vector<float> X;
+        std::vector<int> row_i, row_t, row_d;
+        for (int i = 0; i < count; ++i) {
+            if (cls[i] < 0) continue;
+            for (int t = 0; t < (int)tiles.size(); ++t)
+                for (int d = 0; d <= batched_max_depth(M[i], N[i], K[i]); ++d) {
+                    float f[6];
+                    raw_features(M[i], N[i], K[i], d, tiles[t], (int)o.precision, f);
+                    for (int j = 0; j < 6; ++j) X.push_back((f[j] - g_model.mean[j]) / g_model.stdv[j]);
+                    row_i.push_back(i); row_t.push_back(t); row_d.push_back(d);
+                }
+        }
+        const int rows = (int)row_i.size();
+        float* dX = reinterpret_cast<float*>(scratch);
+        float* dY = dX + align_up((size_t)rows * 6, 64);
+        float* dP = dY + align_up((size_t)rows, 64);
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            FMM_CUDA(cudaMemcpyAsync(dP, g_model.params, sizeof(float) * FMM_MLP_NPARAM, cudaMemcpyHostToDevice, stream));
+        }
+        FMM_CUDA(cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, stream));
+        FMM_CUDA(mlp_forward(dP, dX, dY, rows, stream));
+        std::vector<float> Y(rows);
+        FMM_CUDA(cudaMemcpyAsync(Y.data(), dY, sizeof(float) * rows, cudaMemcpyDeviceToHost, stream));
+        FMM_CUDA(cudaStreamSynchronize(stream));
+        // predicted ms of problem i at (tile t, depth d); ties: smaller depth, larger tile
+        const int nd = 5, nt = (int)tiles.size();
+        std::vector<double> pms((size_t)count * nt * nd, 0.0);
+        for (int r = 0; r < rows; ++r) pms[((size_t)row_i[r] * nt + row_t[r]) * nd + row_d[r]] = std::exp((double)Y[r]);
+        double best_total = 1e300;
+        std::vector<int> best_cd(nclasses, 0);
+        for (int t = 0; t < (int)tiles.size(); ++t) {
+            double total = 0.0;
+            std::vector<int> cd(nclasses, 0);
+            for (int c = 0; c < nclasses; ++c) {
+                double bd = 1e300;
+                for (int d = 0; d <= cmax[c]; ++d) {
+                    // a depth the deepest member can take but a shallower one cannot
+                    // is predicted at the member's own limit, as it would run
+                    double v = 0.0;
+                    for (int i = 0; i < count; ++i)
+                        if (cls[i] == c)
+                            v += pms[((size_t)i * nt + t) * nd + std::min(d, batched_max_depth(M[i], N[i], K[i]))];
+                    if (v < bd * (1.0 - 1e-6)) { bd = v; cd[c] = d; }
+                }
+                total += bd;
+            }
+            if (total < best_total * (1.0 - 1e-6)) { best_total = total; best_cd = cd; tile = tiles[t]; }
+        }
+        for (int i = 0; i < count; ++i)
+            if (cls[i] >= 0) depth[i] = std::min(best_cd[cls[i]], batched_max_depth(M[i], N[i], K[i]));
+        return FMM_OK;
+    }
+    // exhaustive: whole-batch timings on scratch outputs
+    BatchedTuner T;
+    T.count = count; T.M = M; T.N = N; T.K = K; T.lda = lda; T.ldb = ldb; T.A = A; T.B = B; T.alpha = alpha;
+    T.o = o; T.region = ws; T.num_sms = num_sms; T.stream = stream;
+    T.Cs.assign(count, nullptr);
+    T.ldc.assign(count, 1);
+    T.zeros.assign(count, 0.0f);
+    {
+        Carver cv(scratch);
+        for (int i = 0; i < count; ++i) {
+            T.ldc[i] = std::max<int64_t>(N[i], 1);
+            T.Cs[i] = cv.take<float>((size_t)M[i] * (size_t)T.ldc[i]);
+        }
+    }
+    FMM_CUDA(cudaEventCreate(&T.e0));
+    FMM_CUDA(cudaEventCreate(&T.e1));
+    fmm_status_t s = FMM_OK;
+    float best_total = 1e30f;
+    std::vector<int> best_depth = depth;
+    for (int t = 0; t < (int)tiles.size() && s == FMM_OK; ++t) {
+        std::vector<int> cur = depth;   // start from the fixed rule
+        float cur_ms = 0.f;
+        if ((s = T.time(cur, tiles[t], &cur_ms)) != FMM_OK) break;
+        for (int c : order) {
+            int at = -1;
+            for (int i = 0; i < count; ++i)
+                if (cls[i] == c) { at = cur[i]; break; }
+            for (int d = 0; d <= cmax[c] && s == FMM_OK; ++d) {
+                if (d == at) continue;
+                std::vector<int> trial = with_class_depth(cur, c, d);
+                float ms = 0.f;
+                if ((s = T.time(trial, tiles[t], &ms)) != FMM_OK) break;
+                if (ms < 0.99f * cur_ms) { cur = trial; cur_ms = ms; at = d; }
+            }
+            if (s != FMM_OK) break;
+        }
+        if (s == FMM_OK && cur_ms < best_total) { best_total = cur_ms; best_depth = cur; tile = tiles[t]; }
+    }
+    cudaEventDestroy(T.e0);
+    cudaEventDestroy(T.e1);
+    if (s != FMM_OK) return s;
+    depth = best_depth;
+    return FMM_OK;
+}
+
+// Workspace of a batched plan: the largest plan any candidate configuration
+// builds (each problem at its most demanding depth, the larger tile's tables),
+// then, for EXHAUSTIVE / MLP, scratch outputs and inference buffers.
+fmm_status_t batched_need(int count, const int64_t* M, const int64_t* N, const int64_t* K, const int64_t* lda,
+                          const int64_t* ldb, const int64_t* ldc, const float* alpha, const float* beta,
+                          const fmm_options_t& o, size_t* region, size_t* total) {
+    fmm_status_t s;
+    std::vector<int> dfix(count);
+    for (int i = 0; i < count; ++i) dfix[i] = batched_fixed_depth(M[i], N[i], K[i], alpha[i], o);
+    const bool tune = o.planner != FMM_PLANNER_FIXED && o.depth < 0;
+    size_t r = 0;
+    const std::vector<int> tiles = tune ? batched_tiles(o) : std::vector<int>{o.leaf_tile};
+    for (int tile : tiles) {
+        size_t need = 0;
+        fmm_batched_s tmp;
+        if ((s = batched_build(&tmp, count, M, N, K, nullptr, lda, nullptr, ldb, nullptr, ldc, alpha, beta, o, nullptr,
+                               &need, dfix.data(), tile)) != FMM_OK)
+            return s;
+        r = std::max(r, need);
+        if (!tune) continue;
+        // every problem at its most demanding candidate depth, priced one problem at a time
+        size_t sum = 0;
+        for (int i = 0; i < count; ++i) {
+            size_t best = 0;
+            for (int d = 0; d <= batched_max_depth(M[i], N[i], K[i]); ++d) {
+                size_t ni = 0;
+                fmm_batched_s one;
+                if ((s = batched_build(&one, 1, M + i, N + i, K + i, nullptr, lda + i, nullptr, ldb + i, nullptr,
+                                       ldc + i, alpha + i, beta + i, o, nullptr, &ni, &d, tile)) != FMM_OK)
+                    return s;
+                best = std::max(best, ni);
+            }
+            sum += best;
+        }
+        r = std::max(r, sum + (size_t)count * 4096 + (1u << 20));
+    }
+    *region = align_up(r, 256);
+    size_t t = *region;
+    if (tune) {
+        size_t c = 0;
+        for (int i = 0; i < count; ++i) c += align_up((size_t)M[i] * (size_t)std::max<int64_t>(N[i], 1) * 4, 256);
+        size_t rows = 0;
+        for (int i = 0; i < count; ++i) rows += (size_t)(batched_max_depth(M[i], N[i], K[i]) + 1) * 2;
+        const size_t io = (align_up(rows * 6, 64) + align_up(rows, 64) + FMM_MLP_NPARAM) * 4 + 1024;
+        t += std::max(c, io);
+    }
+    *total = align_up(t, 256);
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fmm_status_t fmm_batched_plan(fmm_batched_t* out, int count, const int64_t* M, const int64_t* N, const int64_t* K,
+                              const float* const* A, const int64_t* lda, const float* const* B, const int64_t* ldb,
+                              float* const* C, const int64_t* ldc, const float* alpha, const float* beta,
+                              const fmm_options_t* opt, void* workspace, size_t workspace_bytes,
+                              size_t* workspace_needed, fmm_stream_t stream) {
+    if (out) *out = nullptr;
+    fmm_status_t s = batched_check(count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, opt);
+    if (s != FMM_OK) return s;
+    fmm_options_t o;
+    if (opt) o = *opt; else fmm_options_default(&o);
+    size_t region = 0, need = 0;
+    if ((s = batched_need(count, M, N, K, lda, ldb, ldc, alpha, beta, o, &region, &need)) != FMM_OK) return s;
+    if (workspace_needed) *workspace_needed = need;
+    if (!out) return FMM_OK;
+    DeviceInfo di;
+    if ((s = device_info(&di)) != FMM_OK) return s;
+    if (count > 0 && (!A || !B || !C)) return FMM_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < need) return FMM_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return FMM_ERR_ALIGNMENT;
+    std::vector<int> depth, cls;
+    int nclasses = 0, tile = 0;
+    if ((s = batched_choose(count, M, N, K, A, lda, B, ldb, alpha, o, static_cast<char*>(workspace), region,
+                            di.num_sms, (cudaStream_t)stream, depth, cls, nclasses, tile)) != FMM_OK)
+        return s;
+    fmm_batched_s* b = new (std::nothrow) fmm_batched_s();
+    if (!b) return FMM_ERR_OOM;
+    b->num_sms = di.num_sms;
+    if ((s = batched_build(b, count, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, o, static_cast<char*>(workspace),
+                           nullptr, depth.data(), tile)) != FMM_OK) {
+        delete b;
+        return s;
+    }
+    b->cls = cls;
+    b->nclasses = nclasses;
+    for (auto* q : b->subs) q->num_sms = di.num_sms;
+    *out = b;
+    return FMM_OK;
+}
+
+fmm_status_t fmm_batched_run(fmm_batched_t b, fmm_stream_t stream_) {
+    if (!b) return FMM_ERR_INVALID_ARG;
+    return batched_run(b, (cudaStream_t)stream_);
+}
+
 void fmm_batched_free(fmm_batched_t b) { delete b; }
+
+fmm_status_t fmm_batched_classes(fmm_batched_t b, int* classes, int* nclasses, int* leaf_tile) {
+    if (!b) return FMM_ERR_INVALID_ARG;
+    if (classes) for (int i = 0; i < b->count; ++i) classes[i] = b->cls.empty() ? -1 : b->cls[i];
+    if (nclasses) *nclasses = b->nclasses;
+    if (leaf_tile) *leaf_tile = b->tile;
+    return FMM_OK;
+}
 
 fmm_status_t fmm_batched_info(fmm_batched_t b, int* depths, int64_t* total_tiles, int64_t* launches) {
     if (!b) return FMM_ERR_INVALID_ARG;

@@ -340,6 +340,8 @@ def _batched_argtypes():
     _lib.fmm_batched_free.restype = None
     _lib.fmm_batched_info.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     _lib.fmm_batched_info.restype = C.c_int
+    _lib.fmm_batched_classes.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    _lib.fmm_batched_classes.restype = C.c_int
 
 
 _batched_argtypes()
@@ -382,7 +384,11 @@ class BatchedPlan:
         d = (C.c_int * max(self.count, 1))()
         t, l = C.c_int64(), C.c_int64()
         _check(_lib.fmm_batched_info(self.handle, d, C.byref(t), C.byref(l)), "fmm_batched_info")
-        return dict(depths=list(d)[: self.count], total_tiles=t.value, launches=l.value)
+        cl = (C.c_int * max(self.count, 1))()
+        nc, tile = C.c_int(), C.c_int()
+        _check(_lib.fmm_batched_classes(self.handle, cl, C.byref(nc), C.byref(tile)), "fmm_batched_classes")
+        return dict(depths=list(d)[: self.count], total_tiles=t.value, launches=l.value,
+                    classes=list(cl)[: self.count], nclasses=nc.value, leaf_tile=tile.value)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -428,6 +434,11 @@ def fmm_batched_run(bplan, stream=None):
 
 def fmm_batched_info(bplan):
     return bplan.info()
+
+
+def fmm_batched_classes(bplan):
+    i = bplan.info()
+    return dict(classes=i["classes"], nclasses=i["nclasses"], leaf_tile=i["leaf_tile"])
 
 
 def fmm_batched_free(bplan):

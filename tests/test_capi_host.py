@@ -230,3 +230,23 @@ def test_fuse_last_option_validated(F):
     for bad in (2, -2):
         o = F.options(fuse_last=bad)
         assert F.library().fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 1
+
+
+def test_batched_planner_workspace_includes_scratch_outputs(F):
+    # the exhaustive batched planner times whole-batch launches on scratch
+    # outputs in the workspace: its query covers the fixed plan plus them
+    shapes = [(512, 256, 384), (1024, 1024, 1024), (300, 700, 128)]
+    n = len(shapes)
+    i64 = C.c_int64 * n
+    arrs = (i64(*[m for m, k, nn in shapes]), i64(*[nn for m, k, nn in shapes]), i64(*[k for m, k, nn in shapes]),
+            None, i64(*[k for m, k, nn in shapes]), None, i64(*[nn for m, k, nn in shapes]), None,
+            i64(*[nn for m, k, nn in shapes]), (C.c_float * n)(*[1.0] * n), (C.c_float * n)(*[0.0] * n))
+    need = {}
+    for pl in ("fixed", "exhaustive", "mlp"):
+        o = F.options(planner=pl)
+        sz = C.c_size_t(0)
+        assert F.library().fmm_batched_plan(None, n, *arrs, C.byref(o), None, 0, C.byref(sz), None) == 0
+        need[pl] = sz.value
+    outputs = sum(m * nn * 4 for m, k, nn in shapes)
+    assert need["exhaustive"] >= need["fixed"] + outputs
+    assert need["mlp"] == need["exhaustive"]

@@ -146,3 +146,102 @@ def test_one_shot_gemm_batched_and_unsupported_forms(F):
         with pytest.raises(F.FmmError) as e:
             F.fmm_gemm_batched(As, Bs, Cs, **kw)
         assert e.value.status == 6
+
+
+def _max_depth(m, k, n):
+    # the library's limit for a batched problem: depth <= 4, leaves >= 64 wide
+    d = 4
+    while d > 0 and (min(m, k, n) >> d) < 64:
+        d -= 1
+    return d
+
+
+def _replay_ms(torch, bp, reps=5):
+    bp.run()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        s.record()
+        bp.run()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return sorted(ts)[len(ts) // 2]
+
+
+def test_batched_exhaustive_planner_per_class(F):
+    # the library's own tuner: one depth per size class, whole-batch timings;
+    # the plan it keeps is no slower than the fixed rule's, and exact on integers
+    import torch
+    probs = _problems(64, 9700, lo=128, hi=2048, mult=4)
+    As, Bs, Cs = _upload(probs)
+    fixed = F.BatchedPlan(As, Bs, Cs, planner="fixed")
+    t_fixed = _replay_ms(torch, fixed)
+    fixed.close()
+    bp = F.BatchedPlan(As, Bs, Cs, planner="exhaustive")
+    info = bp.info()
+    by_class = {}
+    for i, (A, B) in enumerate(probs):
+        c = info["classes"][i]
+        assert 0 <= c < info["nclasses"]
+        m, k = A.shape
+        n = B.shape[1]
+        d = info["depths"][i]
+        # members of a class share its depth, except where a member's own limit caps it
+        by_class.setdefault(c, set()).add(d if d < _max_depth(m, k, n) else -1)
+    assert all(len({x for x in v if x >= 0}) <= 1 for v in by_class.values())
+    for c in Cs:
+        c.fill_(float("nan"))
+    t_ex = _replay_ms(torch, bp)
+    for (A, B), Cd in zip(probs, Cs):
+        ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+        assert np.array_equal(Cd.cpu().numpy(), ref)
+    assert t_ex <= 1.10 * t_fixed, (t_ex, t_fixed)
+    bp.close()
+
+
+def _depth_preferring_model(F):
+    # a hand-set cost model: predicted log(ms) = 5 - depth + 0.5 * (tile / 128),
+    # features unstandardised, so the MLP planner must take every class to its
+    # deepest level and the 256-wide tile
+    p = np.zeros(F.NPARAM, dtype=np.float32)
+    W1 = p[0:384].reshape(64, 6)
+    W2 = p[448:448 + 4096].reshape(64, 64)
+    W3 = p[448 + 4096 + 64:448 + 4096 + 64 + 64]
+    W1[0, 3] = 1.0          # h1_0 = relu(depth)
+    W1[1, 4] = 1.0          # h1_1 = relu(tile / 128)
+    W2[0, 0] = 1.0
+    W2[1, 1] = 1.0
+    W3[0] = -1.0
+    W3[1] = 0.5
+    p[-1] = 5.0
+    return p, np.zeros(6, np.float32), np.ones(6, np.float32)
+
+
+def test_batched_mlp_planner_follows_the_model(F):
+    import torch
+    probs = _problems(40, 9800, lo=128, hi=1500, mult=4)
+    As, Bs, Cs = _upload(probs)
+    params, mean, std = _depth_preferring_model(F)
+    F.fmm_set_cost_model(params, mean, std)
+    try:
+        bp = F.BatchedPlan(As, Bs, Cs, planner="mlp")
+    finally:
+        F.fmm_set_cost_model(None)
+    info = bp.info()
+    assert info["leaf_tile"] == 256
+    fixed_depths = F.BatchedPlan(As, Bs, Cs, planner="fixed").info()["depths"]
+    changed = 0
+    for i, (A, B) in enumerate(probs):
+        m, k = A.shape
+        n = B.shape[1]
+        assert info["depths"][i] == _max_depth(m, k, n)
+        changed += info["depths"][i] != fixed_depths[i]
+    assert changed > 0
+    bp.run()
+    torch.cuda.synchronize()
+    for (A, B), Cd in zip(probs, Cs):
+        ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+        assert np.array_equal(Cd.cpu().numpy(), ref)
+    bp.close()

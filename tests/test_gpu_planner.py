@@ -93,13 +93,17 @@ def test_autotune_and_exhaustive_planner(F):
 
 
 def test_learned_planner_end_to_end(F):
+    # the trained network must beat the method without it: on 60 unseen shapes
+    # the plans it picks take less total time than the fixed-threshold rule's
+    # (both looked up in the same table of measured candidate times), and stay
+    # within 25 % of the exhaustive best
     from paper_1205_2927_gb300 import inputs as I
     from paper_1205_2927_gb300 import planner as PL
-    train_shapes = I.batched_shapes(90, 7100, lo=256, hi=4096, multiple=4)
-    test_shapes = I.batched_shapes(25, 7200, lo=256, hi=4096, multiple=4)
+    train_shapes = I.batched_shapes(200, 7100, lo=256, hi=4096, multiple=4)
+    test_shapes = I.batched_shapes(60, 7200, lo=256, hi=4096, multiple=4)
     recs = PL.collect(train_shapes, reps=1, seed=1)
     X, y = PL.features(recs)
-    params, mean, std, losses = PL.train(X, y, steps=800, lr=3e-3)
+    params, mean, std, losses = PL.train(X, y, steps=1500, lr=3e-3)
     assert losses[-1][1] < 0.1 * float(np.var(y))
     PL.register(params, mean, std)
     try:
@@ -109,4 +113,5 @@ def test_learned_planner_end_to_end(F):
     s = PL.summary(ev)
     print(s)
     assert s["regret_mlp"] <= 0.25
-    assert s["total_ms_mlp"] <= 1.05 * s["total_ms_fixed"]
+    assert s["total_ms_mlp"] < s["total_ms_fixed"], s
+    assert s["gain_over_fixed"] > 0.0
