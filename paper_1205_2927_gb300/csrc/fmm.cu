@@ -1071,7 +1071,7 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
         } else if (d == 0) {
             const long long ldt = rup(K[i], 4);
             float* Bt = cv.take<float>((size_t)N[i] * ldt);
-            const float* Aop = A[i];
+            const float* Aop = A ? A[i] : nullptr;   // A is null in a size query
             long long la = lda[i];
             float* Acopy = nullptr;
             if (!A || (reinterpret_cast<uintptr_t>(A[i]) & 15) || (lda[i] % 4)) {  // size query: assume a copy

@@ -250,3 +250,19 @@ def test_batched_planner_workspace_includes_scratch_outputs(F):
     outputs = sum(m * nn * 4 for m, k, nn in shapes)
     assert need["exhaustive"] >= need["fixed"] + outputs
     assert need["mlp"] == need["exhaustive"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("planner", ["fixed", "exhaustive"])
+def test_batched_size_query_with_null_operand_arrays(F, prec, planner):
+    # the header allows A, B, C == NULL in a size query: no operand array is read
+    shapes = [(100, 50, 60), (700, 640, 512), (16, 3000, 9)]
+    n = len(shapes)
+    i64 = C.c_int64 * n
+    arrs = (i64(*[m for m, k, nn in shapes]), i64(*[nn for m, k, nn in shapes]), i64(*[k for m, k, nn in shapes]),
+            None, i64(*[k for m, k, nn in shapes]), None, i64(*[nn for m, k, nn in shapes]), None,
+            i64(*[nn for m, k, nn in shapes]), (C.c_float * n)(*[1.0] * n), (C.c_float * n)(*[0.0] * n))
+    o = F.options(precision=prec, planner=planner, cutoff=64)
+    sz = C.c_size_t(0)
+    assert F.library().fmm_batched_plan(None, n, *arrs, C.byref(o), None, 0, C.byref(sz), None) == 0
+    assert sz.value > 0
