@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="square",
-                    choices=["square", "single1024", "sweep", "large", "rmul", "split", "batched", "planner",
-                             "residual"],
+                    choices=["square", "single1024", "sweep", "fine_sweep", "large", "rmul", "split", "batched",
+                             "planner", "residual"],
                     help="square: the headline line; the others measure the other configurations")
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     ap.add_argument("--model-out", default=None,
@@ -350,6 +350,36 @@ def wl_sweep(args):
             torch.cuda.empty_cache()
 
 
+def wl_fine_sweep(args):
+    """Square n from 4096 to 20480 in steps of 256, U[-1,1], device-resident FP32:
+    the classical GEMM (depth 0) and Winograd at depths 1-3 where every leaf
+    dimension stays >= 1024, CUDA-event median of 3 calls after 1 warm-up.  The
+    rows show how much of a saw-tooth over n remains (leaf-tile quantisation,
+    padding to the level granule, the choice of depth)."""
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    for n in range(4096, 20480 + 1, 256):
+        A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(2, 40 + n // 256))
+        dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+        dC = torch.empty((n, n), device="cuda")
+        rec = {"workload": "fine_sweep", "n": n}
+        for d in range(0, 4):
+            if d > 0 and (n >> d) < 1024:
+                break
+            p = fmm.Plan(n, n, n, depth=d)
+            ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 1)
+            assert p.device_status() == 0
+            p.close()
+            rec[f"d{d}_ms"] = round(ms, 3)
+            rec[f"d{d}_tflops"] = round(2.0 * n ** 3 / ms / 1e9, 1)
+        best = min((rec[f"d{d}_ms"], d) for d in range(4) if f"d{d}_ms" in rec)
+        rec["best_depth"] = best[1]
+        rec["speedup_vs_d0"] = round(rec["d0_ms"] / best[0], 3)
+        emit(args, rec)
+        del dA, dB, dC
+        torch.cuda.empty_cache()
+
+
 def wl_large(args):
     """n = 32768 (4.3 GB per matrix), U[-1,1], device-resident, depth 0 (classical) and the
     deep plans where the additions' n^2 cost falls behind the leaves' n^3 work; CUDA-event
@@ -545,7 +575,7 @@ def wl_planner(args):
                                                                            for k, v in s.items()}})
 
 
-WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "large": wl_large, "rmul": wl_rmul, "split": wl_split,
+WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "fine_sweep": wl_fine_sweep, "large": wl_large, "rmul": wl_rmul, "split": wl_split,
              "batched": wl_batched,
              "planner": wl_planner, "residual": wl_residual}
 

@@ -518,3 +518,11 @@ def test_mlp_forward_planted_mistakes_are_caught():
 
     for bad in (no_second_relu, w2_transposed):
         assert np.max(np.abs(bad(X) - want)) > 0.1
+
+
+def test_mlp_loss_closed_form():
+    theta = _hand_network()
+    X = _hand_inputs()
+    t = np.array([0.5, -1.0, 2.0, 0.0, 1.25])
+    y = np.array([_hand_output(x) for x in X.tolist()])
+    assert O.mlp_loss(theta, X, t) == pytest.approx(0.5 * float(np.mean((y - t) ** 2)), abs=1e-14)
