@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     ap.add_argument("--model-out", default=None,
                     help="planner workload: write the trained cost model to this file")
+    ap.add_argument("--sizes", default=None, help="fine_sweep: comma-separated sizes instead of 4096..20480 step 256")
+    ap.add_argument("--odd", default="pad", choices=["pad", "peel", "tile"],
+                    help="fine_sweep: odd-size mode of the Winograd plans")
     ap.add_argument("--model-in", default=None,
                     help="batched workload: a trained cost model (planner workload's --model-out) for the learned planner")
     return ap.parse_args()
@@ -358,15 +361,16 @@ def wl_fine_sweep(args):
     padding to the level granule, the choice of depth)."""
     import torch
     from paper_1205_2927_gb300 import fmm, inputs
-    for n in range(4096, 20480 + 1, 256):
+    sizes = [int(x) for x in args.sizes.split(",")] if args.sizes else list(range(4096, 20480 + 1, 256))
+    for n in sizes:
         A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(2, 40 + n // 256))
         dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
         dC = torch.empty((n, n), device="cuda")
-        rec = {"workload": "fine_sweep", "n": n}
+        rec = {"workload": "fine_sweep", "n": n, "odd": args.odd}
         for d in range(0, 4):
             if d > 0 and (n >> d) < 1024:
                 break
-            p = fmm.Plan(n, n, n, depth=d)
+            p = fmm.Plan(n, n, n, depth=d, odd=args.odd if d > 0 else "pad")
             ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 1)
             assert p.device_status() == 0
             p.close()

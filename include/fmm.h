@@ -67,7 +67,11 @@ typedef enum {
 
 typedef enum {
     FMM_ODD_PAD = 0,  /* virtual zero padding of the bottom/right quadrants (Eq. 1) */
-    FMM_ODD_PEEL = 1  /* even core through the recursion + classical border fix-ups */
+    FMM_ODD_PEEL = 1, /* even core through the recursion + classical border fix-ups */
+    FMM_ODD_TILE = 2  /* peeling with whole leaf tiles: the recursion covers the largest
+                         multiple of (leaf tile x 2^depth) in M and N (256 x 2^depth for CTA
+                         pairs), so every leaf is a whole number of tiles; the border rows and
+                         columns (and K's remainder modulo 4 x 2^depth) run as classical leaves */
 } fmm_odd_t;
 
 typedef enum {

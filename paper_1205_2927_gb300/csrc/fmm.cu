@@ -165,6 +165,9 @@ struct fmm_plan_s {
     long long M0, K0, N0;     // padded root sizes (Winograd)
     long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
     int peel = 0;
+    // peel granule of M and N (K: 4 * 2^d): 4 * 2^d, or a whole leaf tile
+    // times 2^d for FMM_ODD_TILE
+    long long peel_gm = 0, peel_gn = 0;
     float border_beta = 0.f;
     // pre-split plans: the leaf operands are written as hi / lo planes (SplitKind)
     int pre16 = 0;
@@ -292,9 +295,10 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
     } else {
         const long long g = 4LL << d;
         if (p->peel) {
-            p->Mw = p->M / g * g;
+            const long long gm = p->peel_gm ? p->peel_gm : g, gn = p->peel_gn ? p->peel_gn : g;
+            p->Mw = p->M / gm * gm;
             p->Kw = p->K / g * g;
-            p->Nw = p->N / g * g;
+            p->Nw = p->N / gn * gn;
             p->M0 = p->Mw;
             p->K0 = p->Kw;
             p->N0 = p->Nw;
@@ -378,7 +382,7 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->leaf_tile != 0 && o->leaf_tile != 128 && o->leaf_tile != 256 && o->leaf_tile != 512)
         return FMM_ERR_INVALID_ARG;
     if (o->precision < FMM_PREC_FP32 || o->precision > FMM_PREC_FP16X3) return FMM_ERR_INVALID_ARG;
-    if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL) return FMM_ERR_INVALID_ARG;
+    if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL && o->odd != FMM_ODD_TILE) return FMM_ERR_INVALID_ARG;
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
     if (o->algo == FMM_ALGO_CLASSICAL && o->host_operands) return FMM_ERR_UNSUPPORTED;
@@ -1210,10 +1214,20 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
         t.rmul = t.depth;
         t.depth = 0;
     }
-    t.peel = (o.odd == FMM_ODD_PEEL) ? 1 : 0;
+    t.peel = (o.odd == FMM_ODD_PEEL || o.odd == FMM_ODD_TILE) ? 1 : 0;
+    t.peel_gm = t.peel_gn = 0;
     if (t.peel && t.depth > 0) {
         const long long g = 4LL << t.depth;
         if (M / g == 0 || N / g == 0 || K / g == 0) t.depth = 0;  // no even core: classical leaf
+    }
+    if (o.odd == FMM_ODD_TILE && t.depth > 0) {
+        // leaves of whole tiles in M and N (pair tiles: 256 x 256; one CTA:
+        // 128 rows x leaf-tile columns); a dimension with no whole-tile core
+        // keeps the 4 * 2^d granule
+        const long long tm = (bn == 512) ? 256 : kBM, tn = (bn == 512) ? 256 : bn;
+        const long long gm = tm << t.depth, gn = tn << t.depth;
+        t.peel_gm = M / gm > 0 ? gm : 0;
+        t.peel_gn = N / gn > 0 ? gn : 0;
     }
     t.bn = bn;
     t.tile_req = bn;

@@ -266,3 +266,18 @@ def test_batched_size_query_with_null_operand_arrays(F, prec, planner):
     sz = C.c_size_t(0)
     assert F.library().fmm_batched_plan(None, n, *arrs, C.byref(o), None, 0, C.byref(sz), None) == 0
     assert sz.value > 0
+
+
+def test_tile_peel_workspace_covers_only_the_whole_tile_core(F):
+    # FMM_ODD_TILE at depth 3 on pair tiles: the recursion covers
+    # floor(n / 2048) * 2048 of M and N; n = 16640 -> a 16384 core (leaves of
+    # 2048 = 8 whole tiles), so its planes are those of n = 16384 at K = 16640's
+    # granule-32 core, with the border's B^T and A copies beside them
+    tile = _query(F, 16640, 16640, 16640, depth=3, leaf_tile=512, odd="tile", fuse_last=-1)
+    pad = _query(F, 16640, 16640, 16640, depth=3, leaf_tile=512, odd="pad", fuse_last=-1)
+    leaves = 343
+    planes = 2 * leaves * 2048 * 2080 * 4 * 2          # both sides, raw + lo, leaf K = 16640 / 8 = 2080
+    products = leaves * 2048 * 2048 * 4
+    border = 2 * 16640 * 16640 * 4                       # B^T and an aligned copy of A
+    assert 0 <= tile - planes - products - border < 256 * 1024, tile - planes - products - border
+    assert tile < pad + border

@@ -455,3 +455,25 @@ def test_rmul_float_and_blas(fmm):
     C, _ = run(fmm, A, B, np.full((n, n), np.nan, np.float32), beta=0.0, depth=2, algo="classical")
     assert np.all(np.isfinite(C))
     assert O.error_metric(C, O.classical(A, B), A, B) <= FP32_BOUND
+
+
+@pytest.mark.parametrize("m,k,n,d,bn", [(2100, 900, 1337, 2, 512), (1300, 1100, 700, 1, 256), (1100, 333, 1500, 1, 512)])
+def test_tile_peel_bit_exact_small_int(fmm, m, k, n, d, bn):
+    # FMM_ODD_TILE: whole-tile core through the recursion, the rest as classical
+    # border leaves; exact on small integers like every other mode
+    A = I.small_int((m, k), 15000 + m + d, r=2)
+    B = I.small_int((k, n), 15100 + n + d, r=2)
+    C, info = run(fmm, A, B, depth=d, precision="fp32", leaf_tile=bn, odd="tile")
+    assert info["depth"] == d and info["odd"] == 2
+    ref = O.classical(A.astype(np.int64), B.astype(np.int64))
+    assert np.array_equal(C, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
+def test_tile_peel_float_bound_and_blas(fmm, prec):
+    m, k, n = 3000, 2600, 2800
+    A, B = I.operands(m, k, n, 15200, "normal")
+    C0 = I.uniform((m, n), 15201)
+    C, _ = run(fmm, A, B, C0, alpha=-1.25, beta=0.5, depth=2, precision=prec, leaf_tile=512, odd="tile")
+    err = O.error_metric(C, O.gemm(-1.25, A, B, 0.5, C0), A, B)
+    assert err <= SPLIT_BOUND[prec], err
