@@ -68,10 +68,13 @@ typedef enum {
 typedef enum {
     FMM_ODD_PAD = 0,  /* virtual zero padding of the bottom/right quadrants (Eq. 1) */
     FMM_ODD_PEEL = 1, /* even core through the recursion + classical border fix-ups */
-    FMM_ODD_TILE = 2  /* peeling with whole leaf tiles: the recursion covers the largest
+    FMM_ODD_TILE = 2, /* peeling with whole leaf tiles: the recursion covers the largest
                          multiple of (leaf tile x 2^depth) in M and N (256 x 2^depth for CTA
                          pairs), so every leaf is a whole number of tiles; the border rows and
                          columns (and K's remainder modulo 4 x 2^depth) run as classical leaves */
+    FMM_ODD_AUTO = 3  /* TILE when each of M and N leaves a remainder of at most a quarter of
+                         its whole-tile granule (and some remainder), else PAD; host-resident
+                         and batched plans pad.  fmm_plan_info reports the mode taken */
 } fmm_odd_t;
 
 typedef enum {
@@ -116,8 +119,9 @@ typedef struct {
 
 typedef struct fmm_plan_s* fmm_plan_t;
 
-/* Fill *opt with defaults: depth -1, cutoff 2048, leaf_tile 0, FP32, PAD,
- * FIXED planner, Winograd, device operands.  Returns FMM_ERR_INVALID_ARG on NULL. */
+/* Fill *opt with defaults: depth -1, cutoff 2048, leaf_tile 0, FP32, AUTO odd
+ * sizes, FIXED planner, Winograd, device operands, fuse_last 0 (the library's
+ * choice).  Returns FMM_ERR_INVALID_ARG on NULL. */
 fmm_status_t fmm_options_default(fmm_options_t* opt);
 
 /* Build a plan for one (M, N, K, lda, ldb, ldc, options) problem.

@@ -165,6 +165,7 @@ struct fmm_plan_s {
     long long M0, K0, N0;     // padded root sizes (Winograd)
     long long Mw, Kw, Nw;     // sizes the recursion covers (all of M, K, N; the even core when peeling)
     int peel = 0;
+    fmm_odd_t odd = FMM_ODD_PAD;   // odd-size mode after resolving FMM_ODD_AUTO
     // peel granule of M and N (K: 4 * 2^d): 4 * 2^d, or a whole leaf tile
     // times 2^d for FMM_ODD_TILE
     long long peel_gm = 0, peel_gn = 0;
@@ -382,11 +383,11 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->leaf_tile != 0 && o->leaf_tile != 128 && o->leaf_tile != 256 && o->leaf_tile != 512)
         return FMM_ERR_INVALID_ARG;
     if (o->precision < FMM_PREC_FP32 || o->precision > FMM_PREC_FP16X3) return FMM_ERR_INVALID_ARG;
-    if (o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_PEEL && o->odd != FMM_ODD_TILE) return FMM_ERR_INVALID_ARG;
+    if (o->odd < FMM_ODD_PAD || o->odd > FMM_ODD_AUTO) return FMM_ERR_INVALID_ARG;
     if (o->planner < FMM_PLANNER_FIXED || o->planner > FMM_PLANNER_MLP) return FMM_ERR_INVALID_ARG;
     if (o->algo != FMM_ALGO_WINOGRAD && o->algo != FMM_ALGO_CLASSICAL) return FMM_ERR_INVALID_ARG;
     if (o->algo == FMM_ALGO_CLASSICAL && o->host_operands) return FMM_ERR_UNSUPPORTED;
-    if (o->host_operands && o->odd != FMM_ODD_PAD) return FMM_ERR_UNSUPPORTED;
+    if (o->host_operands && o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_AUTO) return FMM_ERR_UNSUPPORTED;
     if (o->fuse_last < -1 || o->fuse_last > 1) return FMM_ERR_INVALID_ARG;
     return FMM_OK;
 }
@@ -1192,7 +1193,8 @@ fmm_status_t batched_check(int count, const int64_t* M, const int64_t* N, const 
     if (opt) {
         fmm_status_t s = check_opts(opt);
         if (s != FMM_OK) return s;
-        if (opt->odd != FMM_ODD_PAD || opt->algo == FMM_ALGO_CLASSICAL) return FMM_ERR_UNSUPPORTED;
+        if ((opt->odd != FMM_ODD_PAD && opt->odd != FMM_ODD_AUTO) || opt->algo == FMM_ALGO_CLASSICAL)
+            return FMM_ERR_UNSUPPORTED;
     }
     (void)A; (void)B; (void)C;
     return FMM_OK;
@@ -1214,17 +1216,31 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
         t.rmul = t.depth;
         t.depth = 0;
     }
-    t.peel = (o.odd == FMM_ODD_PEEL || o.odd == FMM_ODD_TILE) ? 1 : 0;
+    // odd sizes: AUTO peels to whole leaf tiles when every peeled dimension's
+    // remainder is at most a quarter of its granule (the last tile row or column
+    // of every leaf would be mostly padding) and pads otherwise; host-resident
+    // plans always pad
+    fmm_odd_t odd = o.odd;
+    const long long tm = (bn == 512) ? 256 : kBM, tn = (bn == 512) ? 256 : bn;
+    if (odd == FMM_ODD_AUTO) {
+        odd = FMM_ODD_PAD;
+        if (!t.host && t.depth > 0 && o.algo == FMM_ALGO_WINOGRAD) {
+            const long long gm = tm << t.depth, gn = tn << t.depth;
+            const long long rm = M % gm, rn = N % gn;
+            if (M >= gm && N >= gn && (rm > 0 || rn > 0) && 4 * rm <= gm && 4 * rn <= gn) odd = FMM_ODD_TILE;
+        }
+    }
+    t.odd = odd;
+    t.peel = (odd == FMM_ODD_PEEL || odd == FMM_ODD_TILE) ? 1 : 0;
     t.peel_gm = t.peel_gn = 0;
     if (t.peel && t.depth > 0) {
         const long long g = 4LL << t.depth;
         if (M / g == 0 || N / g == 0 || K / g == 0) t.depth = 0;  // no even core: classical leaf
     }
-    if (o.odd == FMM_ODD_TILE && t.depth > 0) {
+    if (odd == FMM_ODD_TILE && t.depth > 0) {
         // leaves of whole tiles in M and N (pair tiles: 256 x 256; one CTA:
         // 128 rows x leaf-tile columns); a dimension with no whole-tile core
         // keeps the 4 * 2^d granule
-        const long long tm = (bn == 512) ? 256 : kBM, tn = (bn == 512) ? 256 : bn;
         const long long gm = tm << t.depth, gn = tn << t.depth;
         t.peel_gm = M / gm > 0 ? gm : 0;
         t.peel_gn = N / gn > 0 ? gn : 0;
@@ -1304,6 +1320,7 @@ void raw_features(long long M, long long N, long long K, int depth, int bn, int 
 void make_child(const fmm_plan_s* p, fmm_plan_s& c) {
     fmm_options_t o = p->opt;
     o.host_operands = 0;
+    o.odd = FMM_ODD_PAD;   // the quadrant buffers are padded to the level granule already
     make_tmp(c, p->hm, p->hn, p->hk, p->hk, p->hn, p->hn, o, p->depth > 0 ? p->depth - 1 : 0, p->tile_req);
 }
 
@@ -2012,7 +2029,7 @@ fmm_status_t fmm_options_default(fmm_options_t* o) {
     o->cutoff = 2048;
     o->leaf_tile = 0;
     o->precision = FMM_PREC_FP32;
-    o->odd = FMM_ODD_PAD;
+    o->odd = FMM_ODD_AUTO;
     o->planner = FMM_PLANNER_FIXED;
     o->algo = FMM_ALGO_WINOGRAD;
     o->host_operands = 0;
@@ -2227,7 +2244,7 @@ fmm_status_t fmm_plan_info(fmm_plan_t p, int* depth, int* leaf_tile, int* precis
     if (depth) *depth = p->rmul ? p->rmul : p->depth;
     if (leaf_tile) *leaf_tile = (p->pair || (p->host && p->tile_req == 512)) ? 512 : p->bn;
     if (precision) *precision = (int)p->opt.precision;
-    if (odd) *odd = (int)p->opt.odd;
+    if (odd) *odd = (int)p->odd;
     if (algo) *algo = (int)p->opt.algo;
     return FMM_OK;
 }

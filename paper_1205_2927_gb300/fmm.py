@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_ALIGNMENT", 3
                 4: "FMM_ERR_OOM", 5: "FMM_ERR_CUDA", 6: "FMM_ERR_UNSUPPORTED", 7: "FMM_ERR_TIMEOUT",
                 8: "FMM_ERR_NO_DEVICE", 9: "FMM_ERR_WORKSPACE"}
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16x3": 2, "fp16x3": 3}
-ODD = {"pad": 0, "peel": 1, "tile": 2}
+ODD = {"pad": 0, "peel": 1, "tile": 2, "auto": 3}
 PLANNERS = {"fixed": 0, "exhaustive": 1, "mlp": 2}
 ALGOS = {"winograd": 0, "classical": 1}
 
@@ -107,7 +107,7 @@ def _check(status, where):
         raise FmmError(status, where)
 
 
-def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="pad", planner="fixed",
+def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="auto", planner="fixed",
             algo="winograd", host_operands=0, refine_fp64=0, fuse_last=0) -> Options:
     o = Options()
     _check(_lib.fmm_options_default(C.byref(o)), "fmm_options_default")

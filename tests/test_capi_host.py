@@ -49,7 +49,7 @@ def test_every_declared_symbol_has_a_binding(F):
 
 def test_options_default(F):
     o = F.options()
-    assert (o.depth, o.cutoff, o.leaf_tile, o.precision, o.odd, o.planner, o.algo) == (-1, 2048, 0, 0, 0, 0, 0)
+    assert (o.depth, o.cutoff, o.leaf_tile, o.precision, o.odd, o.planner, o.algo) == (-1, 2048, 0, 0, 3, 0, 0)
 
 
 def test_status_strings(F):
@@ -281,3 +281,21 @@ def test_tile_peel_workspace_covers_only_the_whole_tile_core(F):
     border = 2 * 16640 * 16640 * 4                       # B^T and an aligned copy of A
     assert 0 <= tile - planes - products - border < 256 * 1024, tile - planes - products - border
     assert tile < pad + border
+
+
+@pytest.mark.parametrize("n,d,resolved", [(16640, 3, "tile"), (16896, 3, "tile"), (19000, 3, "pad"),
+                                          (20224, 2, "pad"), (16384, 3, "pad"), (18688, 3, "tile")])
+def test_auto_odd_mode_resolution(F, n, d, resolved):
+    # AUTO peels to whole leaf tiles when each remainder is at most a quarter of
+    # the granule (256 * 2^d on CTA pairs), else pads: its workspace is that mode's
+    auto = _query(F, n, n, n, depth=d, leaf_tile=512, odd="auto")
+    want = _query(F, n, n, n, depth=d, leaf_tile=512, odd=resolved)
+    assert auto == want
+
+
+def test_auto_odd_mode_accepted_by_host_and_batched_plans(F):
+    need = C.c_size_t(0)
+    o = F.options(odd="auto", host_operands=1, depth=1)
+    assert F.library().fmm_plan(None, 1000, 1000, 1000, 1000, 1000, 1000, C.byref(o), None, 0, C.byref(need), None) == 0
+    o = F.options(odd="tile", host_operands=1, depth=1)
+    assert F.library().fmm_plan(None, 1000, 1000, 1000, 1000, 1000, 1000, C.byref(o), None, 0, C.byref(need), None) == 6

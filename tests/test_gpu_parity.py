@@ -477,3 +477,16 @@ def test_tile_peel_float_bound_and_blas(fmm, prec):
     C, _ = run(fmm, A, B, C0, alpha=-1.25, beta=0.5, depth=2, precision=prec, leaf_tile=512, odd="tile")
     err = O.error_metric(C, O.gemm(-1.25, A, B, 0.5, C0), A, B)
     assert err <= SPLIT_BOUND[prec], err
+
+
+def test_auto_odd_mode_takes_tile_peel_when_remainders_are_small(fmm):
+    m, k, n = 2100, 900, 2150      # depth 2 on pairs: granule 1024, remainders 52 and 102
+    A = I.small_int((m, k), 15300, r=2)
+    B = I.small_int((k, n), 15301, r=2)
+    C, info = run(fmm, A, B, depth=2, precision="fp32", leaf_tile=512)
+    assert info["odd"] == 2
+    assert np.array_equal(C, O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32))
+    C2, info2 = run(fmm, A, B, depth=2, precision="fp32", leaf_tile=512, odd="auto")
+    assert info2["odd"] == 2 and np.array_equal(C2, C)
+    _, info3 = run(fmm, A[:, :], B[:, :1500], depth=2, precision="fp32", leaf_tile=512)
+    assert info3["odd"] == 0       # remainder 476 of 1024: padded
