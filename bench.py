@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--model-out", default=None,
                     help="planner workload: write the trained cost model to this file")
     ap.add_argument("--sizes", default=None, help="fine_sweep: comma-separated sizes instead of 4096..20480 step 256")
-    ap.add_argument("--odd", default="pad", choices=["pad", "peel", "tile"],
+    ap.add_argument("--odd", default="auto", choices=["pad", "peel", "tile", "auto"],
                     help="fine_sweep: odd-size mode of the Winograd plans")
     ap.add_argument("--model-in", default=None,
                     help="batched workload: a trained cost model (planner workload's --model-out) for the learned planner")
