@@ -373,9 +373,17 @@ def wl_fine_sweep(args):
             p = fmm.Plan(n, n, n, depth=d, odd=args.odd if d > 0 else "pad")
             ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 1)
             assert p.device_status() == 0
+            taken = p.info["odd"]
             p.close()
             rec[f"d{d}_ms"] = round(ms, 3)
             rec[f"d{d}_tflops"] = round(2.0 * n ** 3 / ms / 1e9, 1)
+            if taken != 0:
+                # the mode taken is not padding: time the padded plan beside it on the same GPU
+                rec[f"d{d}_odd"] = {1: "peel", 2: "tile"}.get(taken, taken)
+                q = fmm.Plan(n, n, n, depth=d, odd="pad")
+                pms = event_ms(torch, lambda: q(dA, dB, dC), 3, 1)
+                q.close()
+                rec[f"d{d}_pad_ms"] = round(pms, 3)
         best = min((rec[f"d{d}_ms"], d) for d in range(4) if f"d{d}_ms" in rec)
         rec["best_depth"] = best[1]
         rec["speedup_vs_d0"] = round(rec["d0_ms"] / best[0], 3)
