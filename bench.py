@@ -489,6 +489,10 @@ def wl_batched(args):
     As = [torch.from_numpy(inputs.uniform((m, k), inputs.seed_for(4, 1) + 3 * i)).cuda() for i, (m, k, n) in enumerate(shapes)]
     Bs = [torch.from_numpy(inputs.uniform((k, n), inputs.seed_for(4, 2) + 3 * i)).cuda() for i, (m, k, n) in enumerate(shapes)]
     Cs = [torch.empty((m, n), device="cuda") for m, k, n in shapes]
+    probe = tensor_peak(fmm, 0, "tf32" if args.precision in ("fp32", "tf32") else "bf16")
+    pk = peaks()[0]
+    tc_products = 1 if args.precision == "tf32" else 3
+    es = 4 if args.precision in ("fp32", "tf32") else 2
     planners = ["fixed", "exhaustive"]
     if args.model_in:
         PL.register(*PL.load(args.model_in))
@@ -517,11 +521,28 @@ def wl_batched(args):
             errs.append(float(np.max(np.abs(Cs[i].cpu().numpy() - ref))) /
                         (float(np.abs(A_h).max()) * float(np.abs(B_h).max()) * A_h.shape[1]))
         depth_hist = {d: int(sum(1 for x in info["depths"] if x == d)) for d in sorted(set(info["depths"]))}
+        # roofline of the replay: tensor work of every leaf (padded to the level
+        # granule, 7^d leaves per recursing problem) against the probe's rate, plus
+        # the split pass of the depth-0 operands and the C writes against HBM
+        leaf_flops, hbm_bytes = 0.0, 0.0
+        for (m, k, n), d in zip(shapes, info["depths"]):
+            g = 4 << d if d > 0 else 1
+            m0, k0, n0 = -(-m // g) * g, -(-k // g) * g, -(-n // g) * g
+            leaf_flops += tc_products * 2.0 * (7 ** d) * (m0 >> d) * (k0 >> d) * (n0 >> d)
+            hbm_bytes += 4.0 * m * n + ((m * k + k * n) * (4 + 2 * es) if d == 0 and args.precision != "tf32"
+                                        else 0.0)
+        t_star = (leaf_flops / (probe["tflops"] * 1e12) + hbm_bytes / (pk["hbm_gbs"] * 1e9)) * 1e3
         emit(args, {"workload": "batched512", "precision": args.precision, "planner": planner,
                     "leaf_tile": info["leaf_tile"], "size_classes": info["nclasses"], "depths": depth_hist,
                     "graph_replay_ms": round(ms, 3), "gflops": round(flops / ms / 1e6, 1), "total_flops": flops,
                     "plan_s": round(plan_s, 2), "leaf_tiles": info["total_tiles"],
-                    "max_error_sampled": max(errs)})
+                    "max_error_sampled": max(errs),
+                    "roofline": {"bound": "tensor", "tensor_tflops_over_replay": round(leaf_flops / ms / 1e9, 1),
+                                 "peak": round(probe["tflops"], 1), "unit": "TFLOP/s",
+                                 "frac": round(leaf_flops / ms / 1e9 / probe["tflops"], 3),
+                                 "leaf_tensor_flops": leaf_flops, "split_and_c_bytes": hbm_bytes,
+                                 "t_star_ms": round(t_star, 3), "t_star_over_measured": round(t_star / ms, 3),
+                                 "model": "leaf flops / probe rate + split and C bytes / HBM copy bandwidth"}})
         del g
         bp.close()
     if args.model_in:
