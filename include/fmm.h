@@ -113,9 +113,10 @@ typedef struct {
                                   of each last-level node are folded into the node's output
                                   quadrants as they complete (the U-chain in its own order, so
                                   the result is bitwise that of the separate post-addition
-                                  pass) and never stored.  Applies to depth-2 and depth-3 plans
+                                  pass) and never stored.  Applies to depth-2 to depth-4 plans
                                   on CTA-pair tiles with split-plane leaves (FP32, BF16X3,
-                                  FP16X3; device operands).  1 on, -1 off, 0 library default */
+                                  FP16X3; device operands).  1 on, -1 off, 0 library default
+                                  (on at depths 2 and 3, off at depth 4) */
 } fmm_options_t;
 
 typedef struct fmm_plan_s* fmm_plan_t;

@@ -342,6 +342,7 @@ void layout(fmm_plan_s* p, char* ws, size_t* needed) {
                 L.cnode = cv.take<float>((size_t)(L.nodes * L.m * L.n));
                 continue;
             }
+            if (p->fused) continue;   // the remaining levels fold straight into C
             if (p->fuse_post() && (l == d - 1 || l == d - 2)) continue;   // fused away
             if (p->fuse_root_post() && l == d - 1) continue;
             if (p->fuse_root_post3()) continue;
@@ -827,7 +828,10 @@ fmm_status_t winograd_post(fmm_plan_s* p, float alpha, float beta, float* C, cud
         // the leaf launch left the level-(d-1) node outputs: the remaining levels
         // straight into the caller's C
         const Level& L = lv[d - 1];
-        if (d == 3)
+        if (d == 4)
+            FMM_CUDA(launch_post_add3(L.cnode, L.n, L.m * L.n, 1, L.m, L.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
+                                      stream));
+        else if (d == 3)
             FMM_CUDA(launch_post_add2(L.cnode, L.n, L.m * L.n, 1, L.m, L.n, C, p->ldc, 0, p->Mw, p->Nw, alpha, beta,
                                       stream));
         else
@@ -1266,9 +1270,12 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
                                                   : kLeaf3xTF32P;
     }
     // the fused last level needs the CTA-pair kernel on split planes and a
-    // Winograd depth of 2 or 3 (the node outputs then fold into C in one pass)
-    const bool fusable = t.pair && t.pre16 && !t.host && t.rmul == 0 && (t.depth == 2 || t.depth == 3);
-    t.fused = fusable && (o.fuse_last > 0 || (o.fuse_last == 0 && kFuseLastDefault)) ? 1 : 0;
+    // Winograd depth of 2 to 4 (the node outputs then fold into C in one pass)
+    const bool fusable = t.pair && t.pre16 && !t.host && t.rmul == 0 && t.depth >= 2 && t.depth <= 4;
+    // by default at depths 2 and 3 (n = 16384, depth 3: 0.4-0.5 ms faster per
+    // call); at depth 4 on request (n = 32768: post-additions 8.8 -> 4.8 ms but
+    // the call measured slower, 172-182 against 163-165 ms)
+    t.fused = fusable && (o.fuse_last > 0 || (o.fuse_last == 0 && kFuseLastDefault && t.depth <= 3)) ? 1 : 0;
 }
 
 size_t plan_bytes(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,

@@ -207,17 +207,26 @@ def test_static_status_without_gpu_is_no_device(F):
     assert F.library().fmm_gemm_static_status(None) == 8
 
 
-@pytest.mark.parametrize("n,d,prec,es", [(16384, 3, "fp32", 4), (8192, 2, "fp32", 4), (8192, 3, "fp16x3", 2)])
+@pytest.mark.parametrize("n,d,prec,es", [(16384, 3, "fp32", 4), (8192, 2, "fp32", 4), (8192, 3, "fp16x3", 2),
+                                          (8192, 4, "fp32", 4)])
 def test_fused_workspace_closed_forms(F, n, d, prec, es):
     # fuse_last = 1: the split planes, the level-(d-1) node outputs (7^(d-1)
     # nodes of (2h)^2 floats, h the leaf size) and the running tiles of up to
     # 128 CTA pairs (512 KB each) replace the 7^d leaf products
-    need = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512, fuse_last=1)
+    need = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512, fuse_last=1, odd="pad")
     leaves, h = 7 ** d, n >> d
     planes = 2 * 2 * leaves * h * h * es
     nodes = 7 ** (d - 1) * (2 * h) ** 2 * 4
     running = 128 * 2 * 2 * 128 * 256 * 4
-    assert 0 <= need - planes - nodes - running < 256 * 1024, need - planes - nodes - running
+    # depth 4 keeps the root level's 7 children per side (fp32); the bottom three
+    # levels run as one pass
+    root_children = 2 * 7 * (n // 2) ** 2 * 4 if d == 4 else 0
+    rest = need - planes - nodes - running - root_children
+    assert 0 <= rest < 256 * 1024, rest
+    # the library's default fuses at depths 2 and 3 only
+    default = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512, odd="pad")
+    assert default == (need if d <= 3 else _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512,
+                                                  fuse_last=-1, odd="pad"))
     # options a fused plan cannot take fall back to the unfused schedule
     assert _query(F, n, n, n, depth=1, precision=prec, leaf_tile=512, fuse_last=1) == \
         _query(F, n, n, n, depth=1, precision=prec, leaf_tile=512, fuse_last=-1)

@@ -80,3 +80,17 @@ def test_fused_error_bound_and_smaller_workspace(fmm):
     _, ws_p = run(fmm, A, B, depth=3, precision="fp32", leaf_tile=512, fuse_last=-1)
     assert O.error_metric(C, O.classical(A, B), A, B) <= FP32_BOUND
     assert ws_f < ws_p + 64 * 1024 * 1024 + 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("m,k,n", [(4096, 4096, 4096), (4200, 4100, 4300)])
+def test_fused_depth4_equals_unfused_bitwise(fmm, prec, m, k, n):
+    # depth 4: the leaf launch writes the 343 level-3 node outputs, the
+    # three-level post pass folds them into C
+    A, B = I.operands(m, k, n, 7600 + m % 89)
+    kw = dict(depth=4, precision=prec, leaf_tile=512, odd="pad")
+    fused, _ = run(fmm, A, B, fuse_last=1, **kw)
+    plain, _ = run(fmm, A, B, fuse_last=-1, **kw)
+    assert np.array_equal(fused, plain)
+    bound = 2e-6 if prec == "fp32" else 4.8e-5
+    assert O.error_metric(fused, O.classical(A, B), A, B) <= bound
