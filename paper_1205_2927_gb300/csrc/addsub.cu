@@ -484,7 +484,8 @@ __device__ __forceinline__ void split_store(void* hi_plane, void* lo_plane, long
         l.y = tf32_round_rne(v.y - tf32_trunc(v.y));
         l.z = tf32_round_rne(v.z - tf32_trunc(v.z));
         l.w = tf32_round_rne(v.w - tf32_trunc(v.w));
-        __stcs(reinterpret_cast<float4*>(static_cast<float*>(hi_plane) + o), v);
+        // no hi plane: the leaves read the raw operand itself (hi = x)
+        if (hi_plane) __stcs(reinterpret_cast<float4*>(static_cast<float*>(hi_plane) + o), v);
         __stcs(reinterpret_cast<float4*>(static_cast<float*>(lo_plane) + o), l);
         return;
     }

@@ -527,14 +527,17 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
     const long long ld = p->ld16;
     const float* Aop = A;
     long long lda = p->lda;
+    // FP32 (3xTF32): the hi plane is the raw value, so an aligned A is read in
+    // place and only its lo plane is written
+    const bool a_raw = p->pre16 && bf == kSplitTF32 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 && p->lda % 4 == 0;
     if (p->pre16) {
         const float* scale = p->mode == kLeafFP16x3P ? p->fp16_scale() : nullptr;
-        Stack16 sa{p->a16[0], p->a16[1], ld, 0, 1};
+        Stack16 sa{a_raw ? nullptr : p->a16[0], p->a16[1], ld, 0, 1};
         Stack16 sb{p->b16[0], p->b16[1], ld, 0, 1};
         FMM_CUDA(launch_split16(A, p->lda, p->M, p->K, sa, 0, bf, scale, 0, stream));
         FMM_CUDA(launch_split16(B, p->ldb, p->K, p->N, sb, 1, bf, scale, 1, stream));
         p->launches += 2;
-        p->acct[0] += (double)(p->M * p->K + p->K * p->N) * (4.0 + 2.0 * p->es16());
+        p->acct[0] += (double)(p->M * p->K + p->K * p->N) * (4.0 + 2.0 * p->es16()) - (a_raw ? 4.0 * (double)(p->M * p->K) : 0.0);
     } else {
         FMM_CUDA(launch_transpose(B, p->ldb, p->K, p->N, p->Bt, p->ld_bt, stream));
         p->launches += 1;
@@ -558,9 +561,14 @@ fmm_status_t run_classical(fmm_plan_s* p, float alpha, const float* A, const flo
         if (p->pre16) {
             const size_t off = (size_t)k0 * p->es16();   // bytes; k0 is a multiple of 8
             for (int i = 0; i < 2; ++i) {
-                if ((s = encode_map16(&args.maps[i], static_cast<char*>(p->a16[i]) + off, bf, kc, p->M, 1, ld,
-                                      p->M * ld, kBM, p->pair)) != FMM_OK)
+                if (i == 0 && a_raw) {
+                    if ((s = encode_map16(&args.maps[0], A + k0, bf, kc, p->M, 1, p->lda, p->M * p->lda, kBM,
+                                          p->pair)) != FMM_OK)
+                        return s;
+                } else if ((s = encode_map16(&args.maps[i], static_cast<char*>(p->a16[i]) + off, bf, kc, p->M, 1, ld,
+                                             p->M * ld, kBM, p->pair)) != FMM_OK) {
                     return s;
+                }
                 if ((s = encode_map16(&args.maps[2 + i], static_cast<char*>(p->b16[i]) + off, bf, kc, p->N, 1, ld,
                                       p->N * ld, p->pair ? 128 : p->bn, p->pair)) != FMM_OK)
                     return s;
@@ -1059,13 +1067,23 @@ fmm_status_t batched_build(fmm_batched_s* b, int count, const int64_t* M, const 
             void* bh = cv.take<char>((size_t)N[i] * ld * es);
             void* bl = cv.take<char>((size_t)N[i] * ld * es);
             if (!ws) continue;
-            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], ah, al, ld, 0, (int)((K[i] + 127) / 128), 0, scale_of(i)});
+            // FP32 (3xTF32) planes hold the raw value as hi: an aligned A is read in place
+            // and only its lo plane is written
+            const bool a_raw = b->split_kind == kSplitTF32 && (reinterpret_cast<uintptr_t>(A[i]) & 15) == 0 &&
+                               lda[i] % 4 == 0;
+            sjobs.push_back(SplitJob{A[i], lda[i], M[i], K[i], a_raw ? nullptr : ah, al, ld, 0,
+                                     (int)((K[i] + 127) / 128), 0, scale_of(i)});
             sjobs.push_back(SplitJob{B[i], ldb[i], K[i], N[i], bh, bl, ld, 0, (int)((N[i] + 127) / 128), 1, scale_of(i)});
             fmm_status_t s;
             const int kd = b->split_kind;
             const bool wide = b->pair != 0;              // pair: 128-byte rows, 128 rows of B per CTA
             const int bbox = wide ? 128 : b->bn;
-            if ((s = encode_map16(&maps[nm], ah, kd, K[i], M[i], 1, ld, M[i] * ld, kBM, wide)) != FMM_OK) return s;
+            if (a_raw) {
+                if ((s = encode_map16(&maps[nm], A[i], kd, K[i], M[i], 1, lda[i], M[i] * lda[i], kBM, wide)) != FMM_OK)
+                    return s;
+            } else if ((s = encode_map16(&maps[nm], ah, kd, K[i], M[i], 1, ld, M[i] * ld, kBM, wide)) != FMM_OK) {
+                return s;
+            }
             if ((s = encode_map16(&maps[nm + 1], al, kd, K[i], M[i], 1, ld, M[i] * ld, kBM, wide)) != FMM_OK) return s;
             if ((s = encode_map16(&maps[nm + 2], bh, kd, K[i], N[i], 1, ld, N[i] * ld, bbox, wide)) != FMM_OK) return s;
             if ((s = encode_map16(&maps[nm + 3], bl, kd, K[i], N[i], 1, ld, N[i] * ld, bbox, wide)) != FMM_OK) return s;

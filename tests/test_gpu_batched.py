@@ -245,3 +245,30 @@ def test_batched_mlp_planner_follows_the_model(F):
         ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
         assert np.array_equal(Cd.cpu().numpy(), ref)
     bp.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_batched_aligned_and_unaligned_a(F, prec):
+    # depth-0 problems read an aligned A in place (FP32: only its lo plane is
+    # written); an A that starts off a 16-byte boundary or has an odd row stride
+    # goes through its own planes; both exact on integers
+    import torch
+    shapes = [(300, 257, 190), (128, 640, 512), (77, 129, 301), (512, 512, 512)]
+    probs, As, Bs, Cs = [], [], [], []
+    for i, (m, k, n) in enumerate(shapes):
+        A = I.small_int((m, k + 3), 9900 + i, r=2)
+        B = I.small_int((k, n), 9950 + i, r=2)
+        base = torch.from_numpy(A).cuda()
+        dA = base[:, 1:k + 1] if i % 2 == 0 else base[:, :k]   # offset view: 4-byte aligned only
+        probs.append((A[:, 1:k + 1] if i % 2 == 0 else A[:, :k], B))
+        As.append(dA)
+        Bs.append(torch.from_numpy(B).cuda())
+        Cs.append(torch.full((m, n), float("nan"), device="cuda"))
+    bp = F.BatchedPlan(As, Bs, Cs, precision=prec, cutoff=8192)
+    assert all(d == 0 for d in bp.info()["depths"])
+    bp.run()
+    torch.cuda.synchronize()
+    for (A, B), Cd in zip(probs, Cs):
+        ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+        assert np.array_equal(Cd.cpu().numpy(), ref)
+    bp.close()
