@@ -256,11 +256,15 @@ def test_batched_aligned_and_unaligned_a(F, prec):
     shapes = [(300, 257, 190), (128, 640, 512), (77, 129, 301), (512, 512, 512)]
     probs, As, Bs, Cs = [], [], [], []
     for i, (m, k, n) in enumerate(shapes):
-        A = I.small_int((m, k + 3), 9900 + i, r=2)
         B = I.small_int((k, n), 9950 + i, r=2)
-        base = torch.from_numpy(A).cuda()
-        dA = base[:, 1:k + 1] if i % 2 == 0 else base[:, :k]   # offset view: 4-byte aligned only
-        probs.append((A[:, 1:k + 1] if i % 2 == 0 else A[:, :k], B))
+        if i % 2 == 0:   # a view one element in: 4-byte aligned only, row stride k + 3
+            A = I.small_int((m, k + 3), 9900 + i, r=2)
+            dA = torch.from_numpy(A).cuda()[:, 1:k + 1]
+            A = A[:, 1:k + 1]
+        else:            # contiguous, 16-byte aligned rows (k is a multiple of 4)
+            A = I.small_int((m, k), 9900 + i, r=2)
+            dA = torch.from_numpy(A).cuda()
+        probs.append((A, B))
         As.append(dA)
         Bs.append(torch.from_numpy(B).cuda())
         Cs.append(torch.full((m, n), float("nan"), device="cuda"))
