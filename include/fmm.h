@@ -183,7 +183,9 @@ fmm_status_t fmm_gemm_batched(int count, const int64_t* M, const int64_t* N, con
  *   FMM_PLANNER_MLP: the registered cost model scores every problem at every
  *     candidate (depth, tile) in one inference launch; each class takes the
  *     depth of least predicted sum, the launch the tile of least predicted
- *     total (without a model: EXHAUSTIVE).
+ *     total; that proposal and the fixed rule's plan are then timed as
+ *     whole-batch launches (as EXHAUSTIVE does) and the faster is kept, since
+ *     the model predicts problems run alone (without a model: EXHAUSTIVE).
  * A problem's depth never exceeds 4 or leaves below 64 wide.
  * fmm_batched_run then only launches kernels: one
  * batched transpose/copy launch, the pre-additions of the problems that

@@ -1835,6 +1835,28 @@ fmm_status_t batched_choose(int count, const int64_t* M, const int64_t* N, const
         return r;
     };
     char* scratch = ws + align_up(region_bytes, 256);
+    // whole-batch timings on scratch outputs (the exhaustive search, and the
+    // judge of the cost model's proposal)
+    BatchedTuner T;
+    T.count = count; T.M = M; T.N = N; T.K = K; T.lda = lda; T.ldb = ldb; T.A = A; T.B = B; T.alpha = alpha;
+    T.o = o; T.region = ws; T.num_sms = num_sms; T.stream = stream;
+    T.Cs.assign(count, nullptr);
+    T.ldc.assign(count, 1);
+    T.zeros.assign(count, 0.0f);
+    auto carve_outputs = [&]() {
+        Carver cv(scratch);
+        for (int i = 0; i < count; ++i) {
+            T.ldc[i] = std::max<int64_t>(N[i], 1);
+            T.Cs[i] = cv.take<float>((size_t)M[i] * (size_t)T.ldc[i]);
+        }
+    };
+    struct Events {
+        BatchedTuner& t;
+        ~Events() {
+            if (t.e0) cudaEventDestroy(t.e0);
+            if (t.e1) cudaEventDestroy(t.e1);
+        }
+    } events{T};
     if (o.planner == FMM_PLANNER_MLP && g_model.set) {
         // rows: (problem, tile, depth) for every depth up to the problem's limit
         std::vector<float> X;
@@ -1886,24 +1908,27 @@ fmm_status_t batched_choose(int count, const int64_t* M, const int64_t* N, const
             }
             if (total < best_total * (1.0 - 1e-6)) { best_total = total; best_cd = cd; tile = tiles[t]; }
         }
+        std::vector<int> proposed(depth);
         for (int i = 0; i < count; ++i)
-            if (cls[i] >= 0) depth[i] = std::min(best_cd[cls[i]], batched_max_depth(M[i], N[i], K[i]));
+            if (cls[i] >= 0) proposed[i] = std::min(best_cd[cls[i]], batched_max_depth(M[i], N[i], K[i]));
+        // the model predicts each problem alone; inside one shared launch a level
+        // also costs its own addition launches, so the proposal is timed against
+        // the fixed rule's plan as a whole batch and kept only if faster (the
+        // inference buffers are done with: the outputs reuse that scratch)
+        carve_outputs();
+        FMM_CUDA(cudaEventCreate(&T.e0));
+        FMM_CUDA(cudaEventCreate(&T.e1));
+        const int fixed_tile = o.leaf_tile ? o.leaf_tile : tiles[0];
+        float t_model = 0.f, t_fixed = 0.f;
+        fmm_status_t s;
+        if ((s = T.time(proposed, tile, &t_model)) != FMM_OK) return s;
+        if ((s = T.time(depth, fixed_tile, &t_fixed)) != FMM_OK) return s;
+        if (t_model < t_fixed) depth = proposed;
+        else tile = fixed_tile;
         return FMM_OK;
     }
     // exhaustive: whole-batch timings on scratch outputs
-    BatchedTuner T;
-    T.count = count; T.M = M; T.N = N; T.K = K; T.lda = lda; T.ldb = ldb; T.A = A; T.B = B; T.alpha = alpha;
-    T.o = o; T.region = ws; T.num_sms = num_sms; T.stream = stream;
-    T.Cs.assign(count, nullptr);
-    T.ldc.assign(count, 1);
-    T.zeros.assign(count, 0.0f);
-    {
-        Carver cv(scratch);
-        for (int i = 0; i < count; ++i) {
-            T.ldc[i] = std::max<int64_t>(N[i], 1);
-            T.Cs[i] = cv.take<float>((size_t)M[i] * (size_t)T.ldc[i]);
-        }
-    }
+    carve_outputs();
     FMM_CUDA(cudaEventCreate(&T.e0));
     FMM_CUDA(cudaEventCreate(&T.e1));
     fmm_status_t s = FMM_OK;
@@ -1928,8 +1953,6 @@ fmm_status_t batched_choose(int count, const int64_t* M, const int64_t* N, const
         }
         if (s == FMM_OK && cur_ms < best_total) { best_total = cur_ms; best_depth = cur; tile = tiles[t]; }
     }
-    cudaEventDestroy(T.e0);
-    cudaEventDestroy(T.e1);
     if (s != FMM_OK) return s;
     depth = best_depth;
     return FMM_OK;
