@@ -101,6 +101,18 @@ def test_square_16384_fused_and_unfused_last_level_agree(F):
     assert np.array_equal(fused, plain)
 
 
+def test_16640_depth_3_peeled_to_whole_tiles(F):
+    # the default odd-size mode at a size just above a tile multiple: the
+    # recursion covers 16384 (leaves of 8 whole pair tiles), the 256-wide border
+    # runs as classical leaves
+    n = 16640
+    A, B = I.operands(n, n, n, I.seed_for(2, 65), "normal")
+    C, info = device_run(F, A, B, depth=3)
+    assert (info["depth"], info["odd"]) == (3, 2)
+    rows = sorted(set(sample_rows(n, 3, 5)) | {16383, 16384, 16385, n - 1})
+    check(A, B, C, rows, FP32_BOUND, I.seed_for(2, 94))
+
+
 @pytest.mark.parametrize("odd", ["pad", "peel"])
 def test_odd_19000_depth_2(F, odd):
     n = 19000
