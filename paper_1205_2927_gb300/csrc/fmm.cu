@@ -177,7 +177,7 @@ struct fmm_plan_s {
     int tile_req = 256;  // leaf tile the plan was made for (512: CTA pairs where the precision allows)
     int rmul = 0;        // classical recursion (Table 1) depth; the Winograd depth is then 0
     // the last Winograd level inside the leaf launch (CTA pairs, split planes,
-    // depth 2 or 3): the launch writes the level-(d-1) node outputs, not the
+    // depth 2 to 4): the launch writes the level-(d-1) node outputs, not the
     // 7^d products, through per-pair running tiles (fuse_scratch)
     int fused = 0;
     float* fuse_scratch = nullptr;
