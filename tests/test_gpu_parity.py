@@ -371,9 +371,19 @@ def test_phase_bytes_closed_forms(fmm):
     A = torch.rand(n, n, device="cuda")
     B = torch.rand(n, n, device="cuda")
     C = torch.empty(n, n, device="cuda")
-    # depth 0 (FP32): the operands are read once and written as raw + lo planes
+    # depth 0 (FP32): the operands are read once; B is written as raw + lo
+    # planes, while a 16-byte aligned A serves as its own raw plane and only its
+    # lo plane is written
     p = fmm.Plan(n, n, n, depth=0)
     p(A, B, C)
+    torch.cuda.synchronize()
+    assert p.phase_bytes() == {"pre_bytes": n * n * (4 + 4) + n * n * (4 + 8), "post_bytes": 0}
+    p.close()
+    # an A that starts off the 16-byte grid is split into both planes
+    Aoff = torch.empty(n * n + 1, device="cuda")[1:].view(n, n)
+    Aoff.copy_(A)
+    p = fmm.Plan(n, n, n, depth=0)
+    p(Aoff, B, C)
     torch.cuda.synchronize()
     assert p.phase_bytes() == {"pre_bytes": 2 * n * n * (4 + 8), "post_bytes": 0}
     p.close()
