@@ -15,7 +15,8 @@ Multi-GPU runs are independent replicas (weak scaling): the method has no
 exchange step on one problem, so no collective touches the data path.
 
 ``--impl reference`` times the CPU oracle (``oracle/``) as it stands on the
-host cores, each step a bounded sample (n = 2048) of the same workload.
+host cores, each step a bounded sample of the same workload (one of the seven
+root products of the n = 16384 depth-3 call: n = 8192 at depth 2).
 """
 from __future__ import annotations
 
@@ -52,7 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="square",
                     choices=["square", "single1024", "sweep", "fine_sweep", "large", "rmul", "split", "batched",
-                             "planner", "residual"],
+                             "planner", "residual", "profile_case"],
                     help="square: the headline line; the others measure the other configurations")
     ap.add_argument("--out", default=None, help="also append the JSON lines to this file")
     ap.add_argument("--model-out", default=None,
@@ -60,6 +61,9 @@ def parse():
     ap.add_argument("--sizes", default=None, help="fine_sweep: comma-separated sizes instead of 4096..20480 step 256")
     ap.add_argument("--odd", default="auto", choices=["pad", "peel", "tile", "auto"],
                     help="fine_sweep: odd-size mode of the Winograd plans")
+    ap.add_argument("--fuse-last", type=int, default=0, choices=[-1, 0, 1],
+                    help="profile_case: last Winograd level in the leaf launch (1), separate (-1), library default (0)")
+    ap.add_argument("--calls", type=int, default=3, help="profile_case: calls of the plan")
     ap.add_argument("--model-in", default=None,
                     help="batched workload: a trained cost model (planner workload's --model-out) for the learned planner")
     return ap.parse_args()
@@ -608,7 +612,35 @@ def wl_planner(args):
                                                                            for k, v in s.items()}})
 
 
-WORKLOADS = {"single1024": wl_single1024, "sweep": wl_sweep, "fine_sweep": wl_fine_sweep, "large": wl_large, "rmul": wl_rmul, "split": wl_split,
+def wl_profile_case(args):
+    """One plan (n, depth, leaf tile, fuse_last from the flags; U[-1,1] operands
+    of the headline seed) called `--calls` times, untimed, its device status
+    checked: the launches an ncu capture selects with -k / -s / -c."""
+    import torch
+    from paper_1205_2927_gb300 import fmm, inputs
+    n = args.n
+    A_h, B_h = inputs.operands(n, n, n, inputs.seed_for(2, 0))
+    dA, dB = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+    dC = torch.empty((n, n), device="cuda")
+    kw = {"fuse_last": args.fuse_last}
+    if args.depth >= 0:
+        kw["depth"] = args.depth
+    if args.leaf_tile:
+        kw["leaf_tile"] = args.leaf_tile
+    p = fmm.Plan(n, n, n, precision=args.precision, **kw)
+    for _ in range(args.calls):
+        p(dA, dB, dC)
+    torch.cuda.synchronize()
+    status = p.device_status()
+    info = p.info
+    p.close()
+    if status != 0:
+        raise SystemExit(f"device status {status:#x}")
+    emit(args, {"workload": "profile_case", "n": n, "depth": info["depth"], "leaf_tile": info["leaf_tile"],
+                "fuse_last": info["fuse_last"], "calls": args.calls})
+
+
+WORKLOADS = {"single1024": wl_single1024, "profile_case": wl_profile_case, "sweep": wl_sweep, "fine_sweep": wl_fine_sweep, "large": wl_large, "rmul": wl_rmul, "split": wl_split,
              "batched": wl_batched,
              "planner": wl_planner, "residual": wl_residual}
 
