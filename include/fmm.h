@@ -357,7 +357,7 @@ fmm_status_t fmm_gemm_static(int64_t M, int64_t N, int64_t K, float alpha, const
 fmm_status_t fmm_gemm_static_status(fmm_stream_t stream);
 
 /* Measurement helper, not part of the method: the tensor-pipe rate of this
- * GPU, the ceiling the leaf launches are judged against.  Launches, on
+ * GPU, the ceiling the leaf launches are measured against.  Launches, on
  * `stream`, one CTA pair per two SMs that issues tcgen05.mma back to back on
  * operand tiles held in shared memory, in the leaf kernel's instruction shape
  * (cta_group::2, M = 256, N = 256, K-major operands with 128-byte swizzle):

@@ -23,7 +23,7 @@ Accelerated Matrix Multiplication: OpenCL + APU + GPU + Fast Matrix Multiply"
   post-additions) is used, in the S/T/P/U notation, with odd sizes handled by
   the zero padding implied by Eq. 1 ("pad") or by dynamic peeling ("peel").
 * ``freivalds``/``error_metric``: the residual check and the max-norm error
-  measure used to judge results (the paper itself reports no error analysis,
+  measure that results are held to (the paper itself reports no error analysis,
   Sec. 1, last paragraph).
 * ``split_*``/``split_product``: the hi/lo operand splits of the split-precision
   leaves (three products, fp32 accumulation).

@@ -1836,7 +1836,7 @@ fmm_status_t batched_choose(int count, const int64_t* M, const int64_t* N, const
     };
     char* scratch = ws + align_up(region_bytes, 256);
     // whole-batch timings on scratch outputs (the exhaustive search, and the
-    // judge of the cost model's proposal)
+    // check on the cost model's proposal)
     BatchedTuner T;
     T.count = count; T.M = M; T.N = N; T.K = K; T.lda = lda; T.ldb = ldb; T.A = A; T.B = B; T.alpha = alpha;
     T.o = o; T.region = ws; T.num_sms = num_sms; T.stream = stream;
