@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--fuse-last", type=int, default=0, choices=[-1, 0, 1],
                     help="profile_case: last Winograd level in the leaf launch (1), separate (-1), library default (0)")
     ap.add_argument("--calls", type=int, default=3, help="profile_case: calls of the plan")
+    ap.add_argument("--host-copy", default="default", choices=["default", "engine", "sm"],
+                    help="e2e leg: how host operands cross the link (library default, copy engines, SM copies)")
     ap.add_argument("--model-in", default=None,
                     help="batched workload: a trained cost model (planner workload's --model-out) for the learned planner")
     return ap.parse_args()
@@ -820,12 +822,19 @@ def main():
         pC = torch.empty((n, n), dtype=torch.float32).pin_memory()
         del dC
         wplan.close()
-        hplan = fmm.Plan(n, n, n, depth=depth, precision=args.precision, leaf_tile=bn, host_operands=1)
-        ems = timed(torch, dist, world, lambda: hplan(pA, pB, pC), args.steps, 1)
+        hplan = fmm.Plan(n, n, n, depth=depth, precision=args.precision, leaf_tile=bn, host_operands=1,
+                         host_copy=args.host_copy)
+        # at least 16 warm-up calls (about 450 ms, longer than the period of the
+        # copy-engine stalls some hosts show): the library's default host copies
+        # settle on their path (copy engines, or SM copies once a call's
+        # transfers stalled) before the timed calls, which run ahead of the GPU
+        e2e_warmup = max(args.warmup, 16)
+        ems = timed(torch, dist, world, lambda: hplan(pA, pB, pC), args.steps, e2e_warmup)
         e2e = {"value": round(flops * world / ems / 1e6, 1), "unit": "GFLOPS",
                "h2d_bytes_per_step": int(pA.numel() * 4 + pB.numel() * 4),
                "d2h_bytes_per_step": int(pC.numel() * 4), "ms_per_step": round(ems, 3),
-               "path": "fmm_gemm with pinned host operands (host_operands=1)"}
+               "path": f"fmm_gemm with pinned host operands (host_operands=1, host_copy={args.host_copy})",
+               "warmup": e2e_warmup, "host_copy_after": hplan.host_copy()}
         hplan.close()
 
     # roofline of the dominant kernel (the leaf launch): tensor-pipe TF32 work per launch / time per launch

@@ -117,6 +117,15 @@ typedef struct {
                                   on CTA-pair tiles with split-plane leaves (FP32, BF16X3,
                                   FP16X3; device operands).  1 on, -1 off, 0 library default
                                   (on at depths 2 and 3, off at depth 4) */
+    int host_copy;             /* host-resident plans: how A, B, C cross the host link.
+                                  1: copy engines (cudaMemcpy2DAsync); 2: SM loads and stores
+                                  on the device mapping of the pinned memory (32 blocks; the
+                                  same link rate one way, no duplex, but no stall where the
+                                  copy engines stall; copy engines for memory without a device
+                                  mapping); 0: library default: copy engines until a call's
+                                  input transfers (at least 64 MiB, not the plan's first call)
+                                  ran at under half of the link's rate, SM copies from the
+                                  first call after that judgement (fmm_plan_host_copy) */
 } fmm_options_t;
 
 typedef struct fmm_plan_s* fmm_plan_t;
@@ -254,6 +263,13 @@ fmm_status_t fmm_plan_info(fmm_plan_t plan, int* depth, int* leaf_tile, int* pre
  * outputs (fmm_options_t.fuse_last after the planner ran; for host-resident
  * plans, their device-resident child plan): *fused = 1 or 0. */
 fmm_status_t fmm_plan_fuse_last(fmm_plan_t plan, int* fused);
+
+/* How a host-resident plan moves its next call's operands: *mode = 1 (copy
+ * engines) or 2 (SM loads and stores); 0 for device-resident plans.  Under the
+ * library default (fmm_options_t.host_copy = 0) the answer turns from 1 to 2
+ * once a call's input transfers ran at under half of the host link's rate
+ * (judged at the following call, from calls moving at least 64 MiB in). */
+fmm_status_t fmm_plan_host_copy(fmm_plan_t plan, int* mode);
 
 /* Freivalds residual of a computed product: r = C x - A (B x) for a probe
  * vector x (N entries, device; +-1 entries make a single wrong C entry show up

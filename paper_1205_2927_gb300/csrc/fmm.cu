@@ -210,6 +210,15 @@ struct fmm_plan_s {
     size_t child_ws_bytes = 0;
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t hev[8] = {};
+    // library-default host copies: the input transfers of recent calls that
+    // used the copy engines, each bracketed by a pair of timing events in a
+    // ring, judged at a later call once complete (callers run ahead of the GPU)
+    static constexpr int kJudgeRing = 16;
+    cudaEvent_t hx[kJudgeRing][2] = {};
+    double hx_bytes[kJudgeRing] = {};   // bytes a slot's transfers moved (0: free)
+    int hx_next = 0;
+    long long host_calls = 0;
+    int host_sm_latched = 0;    // the copy engines stalled: SM copies from now on
     // FP16x3: device operand scales {s_a, s_b} and reduction scratch, inside the status block
     float* fp16_scale() const { return scale_override ? scale_override : reinterpret_cast<float*>(status + 16); }
     float* scale_override = nullptr;   // batched sub-plans: the problem's own {s_a, s_b}
@@ -390,6 +399,7 @@ fmm_status_t check_opts(const fmm_options_t* o) {
     if (o->algo == FMM_ALGO_CLASSICAL && o->host_operands) return FMM_ERR_UNSUPPORTED;
     if (o->host_operands && o->odd != FMM_ODD_PAD && o->odd != FMM_ODD_AUTO) return FMM_ERR_UNSUPPORTED;
     if (o->fuse_last < -1 || o->fuse_last > 1) return FMM_ERR_INVALID_ARG;
+    if (o->host_copy < 0 || o->host_copy > 2) return FMM_ERR_INVALID_ARG;
     return FMM_OK;
 }
 
@@ -405,6 +415,17 @@ int leaf_mode(fmm_precision_t p) {
 // Whether plans that can fuse the last Winograd level into the leaf launch do
 // so when the caller leaves fmm_options_t.fuse_last at 0.
 constexpr bool kFuseLastDefault = true;
+
+// Host-resident plans whose caller leaves fmm_options_t.host_copy at 0 use the
+// copy engines (the faster path on a healthy link: duplex, and no SMs taken from
+// the compute) until the input transfers of one call arrive at under half of
+// the link's rate, then SM copies for the rest of the plan's life.  On these
+// GPUs' virtual machines the copy engines can stall for 40-175 ms every few
+// hundred ms after other processes pinned and freed host memory, while SM
+// loads and stores over the same link do not.  Calls moving less than
+// kHostJudgeBytes, and a plan's first call, are not judged.
+constexpr double kHostStallGBs = 100.0;
+constexpr double kHostJudgeBytes = 64.0 * (1 << 20);
 
 // Fixed-threshold planner: one more level while every dimension of the next
 // level's leaves stays at or above the cut-off (the recursion point of Sec. 3.1).
@@ -1360,17 +1381,51 @@ void make_child(const fmm_plan_s* p, fmm_plan_s& c) {
 // after `stream` by events; `stream` waits for the last device-to-host copy.
 fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B, float beta, float* C,
                       cudaStream_t stream) {
-    for (const void* ptr : {(const void*)A, (const void*)B, (const void*)C}) {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-            cudaGetLastError();
-            return FMM_ERR_INVALID_ARG;
-        }
-        if (at.type == cudaMemoryTypeUnregistered) {
-            snprintf(g_last_error, sizeof(g_last_error), "host operands must be page-locked (pinned) memory");
-            return FMM_ERR_INVALID_ARG;
+    // device-side addresses of the three operands (the device mapping of pinned
+    // host memory, or the pointer itself for device memory); null where a
+    // block has none, and then the copy engines move it
+    void* mapped[3] = {nullptr, nullptr, nullptr};
+    {
+        const void* ptrs[3] = {A, B, C};
+        for (int i = 0; i < 3; ++i) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess) {
+                cudaGetLastError();
+                return FMM_ERR_INVALID_ARG;
+            }
+            if (at.type == cudaMemoryTypeUnregistered) {
+                snprintf(g_last_error, sizeof(g_last_error), "host operands must be page-locked (pinned) memory");
+                return FMM_ERR_INVALID_ARG;
+            }
+            mapped[i] = at.devicePointer;
         }
     }
+    const bool mapped_all = mapped[0] && mapped[1] && mapped[2];
+    if (p->opt.host_copy == 0) {
+        // judge the earlier calls' input transfers that have completed
+        for (int i = 0; i < fmm_plan_s::kJudgeRing; ++i) {
+            if (p->hx_bytes[i] <= 0.0) continue;
+            const cudaError_t q = cudaEventQuery(p->hx[i][1]);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();   // a status, not an error of this call
+                continue;
+            }
+            float ms = 0.f;
+            if (q == cudaSuccess && cudaEventElapsedTime(&ms, p->hx[i][0], p->hx[i][1]) == cudaSuccess && ms > 0.f &&
+                p->hx_bytes[i] / ((double)ms * 1e6) < kHostStallGBs)
+                p->host_sm_latched = 1;
+            cudaGetLastError();
+            p->hx_bytes[i] = 0.0;
+        }
+    }
+    const bool sm_copy = mapped_all && (p->opt.host_copy == 2 || (p->opt.host_copy == 0 && p->host_sm_latched));
+    // the library default times this call's input transfers on the copy engines
+    // (in the next ring slot, unless that slot still waits for its call)
+    const int slot = p->hx_next;
+    const bool judge = p->opt.host_copy == 0 && !sm_copy && p->host_calls > 0 && mapped_all &&
+                       p->hx_bytes[slot] <= 0.0;
+    p->host_calls += 1;
+    double in_bytes = 0.0;
     fmm_plan_s* c = p->child;
     cudaEvent_t* ev = p->hev;
     float** q = p->hq;
@@ -1378,12 +1433,22 @@ fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B
     FMM_CUDA(cudaEventRecord(ev[0], stream));
     FMM_CUDA(cudaStreamWaitEvent(p->s_h2d, ev[0], 0));
     FMM_CUDA(cudaStreamWaitEvent(p->s_d2h, ev[0], 0));
+    if (judge) FMM_CUDA(cudaEventRecord(p->hx[slot][0], p->s_h2d));
     // valid part of quadrant (qi, qj) of an R x W host matrix split at (h, w)
-    auto copy = [&](bool to_dev, float* dev, long long ldd, const float* host_c, float* host, long long ldh,
-                    long long R, long long W, long long h, long long w, int qi, int qj) -> fmm_status_t {
+    // host_c / host: the caller's pointer; host_m: its device mapping (SM copies)
+    auto copy = [&](bool to_dev, float* dev, long long ldd, const float* host_c, float* host, const void* host_m,
+                    long long ldh, long long R, long long W, long long h, long long w, int qi, int qj) -> fmm_status_t {
         const long long r0 = qi * h, c0 = qj * w;
         const long long rows = std::min(h, R - r0), cols = std::min(w, W - c0);
         if (rows <= 0 || cols <= 0) return FMM_OK;
+        if (to_dev) in_bytes += 4.0 * (double)(rows * cols);
+        if (sm_copy) {
+            float* hm_ = const_cast<float*>(static_cast<const float*>(host_m)) + r0 * ldh + c0;
+            if (to_dev) FMM_CUDA(launch_host_copy2d(hm_, ldh, dev, ldd, rows, cols, p->s_h2d));
+            else FMM_CUDA(launch_host_copy2d(dev, ldd, hm_, ldh, rows, cols, p->s_d2h));
+            p->launches += 1;
+            return FMM_OK;
+        }
         if (to_dev)
             FMM_CUDA(cudaMemcpy2DAsync(dev, ldd * 4, host_c + r0 * ldh + c0, ldh * 4, cols * 4, rows,
                                        cudaMemcpyHostToDevice, p->s_h2d));
@@ -1392,10 +1457,18 @@ fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B
                                        cudaMemcpyDeviceToHost, p->s_d2h));
         return FMM_OK;
     };
-    auto inA = [&](int i) { return copy(true, q[i], hk, A, nullptr, p->lda, p->M, p->K, hm, hk, i / 2, i % 2); };
-    auto inB = [&](int i) { return copy(true, q[4 + i], hn, B, nullptr, p->ldb, p->K, p->N, hk, hn, i / 2, i % 2); };
-    auto inC = [&](int i) { return copy(true, q[23 + i], hn, C, nullptr, p->ldc, p->M, p->N, hm, hn, i / 2, i % 2); };
-    auto outC = [&](int i) { return copy(false, q[23 + i], hn, nullptr, C, p->ldc, p->M, p->N, hm, hn, i / 2, i % 2); };
+    auto inA = [&](int i) {
+        return copy(true, q[i], hk, A, nullptr, mapped[0], p->lda, p->M, p->K, hm, hk, i / 2, i % 2);
+    };
+    auto inB = [&](int i) {
+        return copy(true, q[4 + i], hn, B, nullptr, mapped[1], p->ldb, p->K, p->N, hk, hn, i / 2, i % 2);
+    };
+    auto inC = [&](int i) {
+        return copy(true, q[23 + i], hn, C, nullptr, mapped[2], p->ldc, p->M, p->N, hm, hn, i / 2, i % 2);
+    };
+    auto outC = [&](int i) {
+        return copy(false, q[23 + i], hn, nullptr, C, mapped[2], p->ldc, p->M, p->N, hm, hn, i / 2, i % 2);
+    };
     fmm_status_t s;
 #define FMM_TRY(x) do { if ((s = (x)) != FMM_OK) return s; } while (0)
     if (p->depth == 0) {
@@ -1403,6 +1476,7 @@ fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B
         FMM_TRY(inB(0));
         if (beta != 0.0f) FMM_TRY(inC(0));
         FMM_CUDA(cudaEventRecord(ev[1], p->s_h2d));
+        if (judge) FMM_CUDA(cudaEventRecord(p->hx[slot][1], p->s_h2d));
         FMM_CUDA(cudaStreamWaitEvent(stream, ev[1], 0));
         FMM_TRY(execute(c, alpha, q[0], q[4], beta, q[23], stream));
         FMM_CUDA(cudaEventRecord(ev[4], stream));
@@ -1426,6 +1500,7 @@ fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B
         FMM_CUDA(cudaEventRecord(ev[5], p->s_h2d));
         if (beta != 0.0f) for (int i = 1; i < 4; ++i) FMM_TRY(inC(i));
         FMM_CUDA(cudaEventRecord(ev[7], p->s_h2d));              // C12, C21, C22 (beta != 0)
+        if (judge) FMM_CUDA(cudaEventRecord(p->hx[slot][1], p->s_h2d));
         float* P[7];
         for (int i = 0; i < 7; ++i) P[i] = q[16 + i];
         QuadPost qp{};
@@ -1463,6 +1538,10 @@ fmm_status_t run_host(fmm_plan_s* p, float alpha, const float* A, const float* B
         p->launches += 6;
     }
 #undef FMM_TRY
+    if (judge && in_bytes >= kHostJudgeBytes) {
+        p->hx_bytes[slot] = in_bytes;
+        p->hx_next = (slot + 1) % fmm_plan_s::kJudgeRing;
+    }
     FMM_CUDA(cudaEventRecord(ev[0], p->s_d2h));
     FMM_CUDA(cudaStreamWaitEvent(stream, ev[0], 0));
     p->launches += c->launches;
@@ -2087,6 +2166,7 @@ fmm_status_t fmm_options_default(fmm_options_t* o) {
     o->host_operands = 0;
     o->refine_fp64 = 0;
     o->fuse_last = 0;
+    o->host_copy = 0;
     return FMM_OK;
 }
 
@@ -2167,6 +2247,8 @@ fmm_status_t fmm_plan(fmm_plan_t* out, int64_t M, int64_t N, int64_t K, int64_t 
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
         for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming);
+        for (int i = 0; i < fmm_plan_s::kJudgeRing * 2 && e == cudaSuccess; ++i)
+            e = cudaEventCreate(&p->hx[i / 2][i % 2]);
         if (e != cudaSuccess) { fmm_free(p); return cuda_fail(e, "host-resident plan setup"); }
     }
     p->last_stream = (cudaStream_t)stream;
@@ -2261,6 +2343,9 @@ void fmm_free(fmm_plan_t p) {
     if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
     for (auto& e : p->hev)
         if (e) cudaEventDestroy(e);
+    for (auto& pair : p->hx)
+        for (auto& e : pair)
+            if (e) cudaEventDestroy(e);
     delete p->child;
     for (auto& es : p->ev_free)
         for (int i = 0; i < 4; ++i) cudaEventDestroy(es.e[i]);
@@ -2282,6 +2367,14 @@ fmm_status_t fmm_wait_selftest(fmm_plan_t p, int64_t limit_ns, fmm_stream_t stre
     cudaStream_t stream = (cudaStream_t)stream_;
     p->last_stream = stream;
     FMM_CUDA(launch_wait_selftest(p->status, (unsigned long long)limit_ns, stream));
+    return FMM_OK;
+}
+
+fmm_status_t fmm_plan_host_copy(fmm_plan_t p, int* mode) {
+    if (!p || !mode) return FMM_ERR_INVALID_ARG;
+    if (!p->host) *mode = 0;
+    else if (p->opt.host_copy) *mode = p->opt.host_copy;
+    else *mode = p->host_sm_latched ? 2 : 1;
     return FMM_OK;
 }
 

@@ -249,5 +249,9 @@ cudaError_t launch_fill(float* p, size_t n, unsigned seed, cudaStream_t stream);
 cudaError_t mlp_forward(const float* params, const float* X, float* Y, int batch, cudaStream_t s);
 // C <- beta * C (beta == 0 writes zeros).
 cudaError_t launch_scale(float* C, long long ldc, long long M, long long N, float beta, cudaStream_t stream);
+// rows x cols block copy by SM loads/stores; either side may be the device
+// mapping of pinned host memory (row strides lds, ldd in elements)
+cudaError_t launch_host_copy2d(const float* src, long long lds, float* dst, long long ldd, long long rows,
+                               long long cols, cudaStream_t stream);
 
 }  // namespace fmm

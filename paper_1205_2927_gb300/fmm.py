@@ -41,7 +41,7 @@ class FmmError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("depth", C.c_int), ("cutoff", C.c_int), ("leaf_tile", C.c_int), ("precision", C.c_int),
                 ("odd", C.c_int), ("planner", C.c_int), ("algo", C.c_int), ("host_operands", C.c_int),
-                ("refine_fp64", C.c_int), ("fuse_last", C.c_int)]
+                ("refine_fp64", C.c_int), ("fuse_last", C.c_int), ("host_copy", C.c_int)]
 
 
 def _load():
@@ -75,6 +75,8 @@ def _load():
     lib.fmm_plan_info.restype = C.c_int
     lib.fmm_plan_fuse_last.argtypes = [vp, C.POINTER(C.c_int)]
     lib.fmm_plan_fuse_last.restype = C.c_int
+    lib.fmm_plan_host_copy.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fmm_plan_host_copy.restype = C.c_int
     lib.fmm_plan_profile.argtypes = [vp, C.c_int]
     lib.fmm_plan_profile.restype = C.c_int
     lib.fmm_plan_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -107,8 +109,11 @@ def _check(status, where):
         raise FmmError(status, where)
 
 
+HOST_COPY = {"default": 0, "engine": 1, "sm": 2}
+
+
 def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="auto", planner="fixed",
-            algo="winograd", host_operands=0, refine_fp64=0, fuse_last=0) -> Options:
+            algo="winograd", host_operands=0, refine_fp64=0, fuse_last=0, host_copy="default") -> Options:
     o = Options()
     _check(_lib.fmm_options_default(C.byref(o)), "fmm_options_default")
     o.depth, o.cutoff, o.leaf_tile = depth, cutoff, leaf_tile
@@ -118,6 +123,7 @@ def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="auto", pl
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.host_operands, o.refine_fp64 = host_operands, refine_fp64
     o.fuse_last = int(fuse_last)
+    o.host_copy = HOST_COPY[host_copy] if isinstance(host_copy, str) else int(host_copy)
     return o
 
 
@@ -161,6 +167,14 @@ def fmm_plan_info(plan):
     vals = [C.c_int() for _ in range(5)]
     _check(_lib.fmm_plan_info(plan, *[C.byref(v) for v in vals]), "fmm_plan_info")
     return dict(zip(("depth", "leaf_tile", "precision", "odd", "algo"), [v.value for v in vals]))
+
+
+def fmm_plan_host_copy(plan):
+    """1: the plan's next call moves host operands with the copy engines, 2: with
+    SM loads and stores, 0: device-resident plan."""
+    m = C.c_int()
+    _check(_lib.fmm_plan_host_copy(plan, C.byref(m)), "fmm_plan_host_copy")
+    return m.value
 
 
 def fmm_plan_fuse_last(plan):
@@ -296,6 +310,10 @@ class Plan:
 
     def profile_read(self):
         return fmm_plan_profile_read(self.handle)
+
+    def host_copy(self):
+        """How the next call moves host operands: "engine", "sm" or None (device plan)."""
+        return {0: None, 1: "engine", 2: "sm"}[fmm_plan_host_copy(self.handle)]
 
     def wait_selftest(self, limit_ns=20_000_000, stream=None):
         """Run the device-wait failure path once (see fmm_wait_selftest)."""

@@ -241,6 +241,19 @@ def test_fuse_last_option_validated(F):
         assert F.library().fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 1
 
 
+def test_host_copy_option_validated(F):
+    # 0 library default, 1 copy engines, 2 SM loads/stores; anything else is rejected
+    need = C.c_size_t(0)
+    assert F.options().host_copy == 0
+    for ok in (0, 1, 2):
+        o = F.options(host_operands=1, host_copy=ok)
+        assert F.library().fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 0
+    for bad in (3, -1):
+        o = F.options(host_operands=1, host_copy=bad)
+        assert F.library().fmm_plan(None, 64, 64, 64, 64, 64, 64, C.byref(o), None, 0, C.byref(need), None) == 1
+    assert F.options(host_copy="sm").host_copy == 2 and F.options(host_copy="engine").host_copy == 1
+
+
 def test_batched_planner_workspace_includes_scratch_outputs(F):
     # the exhaustive batched planner times whole-batch launches on scratch
     # outputs in the workspace: its query covers the fixed plan plus them

@@ -130,3 +130,80 @@ def test_host_resident_ragged_equals_device_resident(F, d):
     assert p.device_status() == 0
     p.close()
     assert np.array_equal(host, dC.cpu().numpy())
+
+
+@pytest.mark.parametrize("m,k,n,d", [(300, 200, 260, 2), (512, 512, 512, 1), (777, 333, 515, 0),
+                                     (1000, 700, 900, 3), (130, 70, 90, 1)])
+def test_host_copy_by_sm_equals_copy_engines(F, m, k, n, d):
+    # the same plan with its host traffic moved by SM loads/stores on the
+    # device mapping of the pinned memory instead of the copy engines: the
+    # device computes the same, so the results agree bit for bit (ragged
+    # quadrants, beta != 0 reads C in)
+    A, B = I.operands(m, k, n, I.seed_for(2, 70 + d), "normal")
+    C0 = I.uniform((m, n), 71 + d)
+    eng = run_host(F, A, B, C0, alpha=0.5, beta=-2.0, depth=d, host_copy="engine")
+    sm = run_host(F, A, B, C0, alpha=0.5, beta=-2.0, depth=d, host_copy="sm")
+    assert np.array_equal(eng, sm)
+    ref = 0.5 * O.classical(A, B) - 2.0 * C0
+    den = float(np.abs(A).max()) * float(np.abs(B).max()) * k
+    assert float(np.max(np.abs(sm - ref))) <= 2e-6 * den + 4.0 * float(np.abs(C0).max()) * 2.0 ** -23
+
+
+def test_host_copy_by_sm_strided_views(F):
+    # pinned views with row strides that are not multiples of 4 (the copy
+    # kernel's element-wise form) and an offset start, exact on integers
+    import torch
+    m, k, n = 301, 203, 257
+    A = I.small_int((m, k), 17001, r=2)
+    B = I.small_int((k, n), 17002, r=2)
+    hA_full = torch.zeros((m, k + 3)).pin_memory()
+    hB_full = torch.zeros((k, n + 5)).pin_memory()
+    hC_full = torch.full((m, n + 1), float("nan")).pin_memory()
+    hA, hB, hC = hA_full[:, 1:k + 1], hB_full[:, 2:n + 2], hC_full[:, :n]
+    hA.copy_(torch.from_numpy(A))
+    hB.copy_(torch.from_numpy(B))
+    for d in (0, 2):
+        launches = {}
+        for how in ("engine", "sm"):
+            hC.fill_(float("nan"))
+            p = F.Plan(m, n, k, lda=k + 3, ldb=n + 5, ldc=n + 1, depth=d, host_operands=1, host_copy=how)
+            p(hA, hB, hC)
+            torch.cuda.current_stream().synchronize()
+            assert p.device_status() == 0
+            launches[how] = p.profile_read()["launches"]
+            p.close()
+            ref = O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float32)
+            assert np.array_equal(hC.numpy(), ref)
+            assert np.all(np.isnan(hC_full[:, n:].numpy()))
+        # the SM form runs one copy kernel per block moved (pinned memory has a
+        # device mapping here), the engine form none
+        assert launches["sm"] > launches["engine"], launches
+
+
+def test_host_copy_mode_query(F):
+    # device plans report none; forced modes report themselves; the library
+    # default starts on the copy engines and may move to SM copies (only if a
+    # call's transfers stalled), with the same results either way
+    import torch
+    n = 4096
+    A, B = I.operands(n, n, n, I.seed_for(2, 80))
+    hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    outs = {}
+    for how in ("default", "engine", "sm"):
+        p = F.Plan(n, n, n, depth=1, host_operands=1, host_copy=how)
+        first = p.host_copy()
+        hC = torch.empty((n, n)).pin_memory()
+        for _ in range(3):
+            p(hA, hB, hC)
+        torch.cuda.current_stream().synchronize()
+        assert p.device_status() == 0
+        if how == "default":
+            assert first == "engine" and p.host_copy() in ("engine", "sm")
+        else:
+            assert first == how and p.host_copy() == how
+        outs[how] = hC.numpy().copy()
+        p.close()
+    assert np.array_equal(outs["default"], outs["engine"]) and np.array_equal(outs["sm"], outs["engine"])
+    d = F.Plan(256, 256, 256)
+    assert d.host_copy() is None
+    d.close()
