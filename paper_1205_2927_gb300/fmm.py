@@ -15,6 +15,7 @@ from . import build as _build
 
 FMM_OK = 0
 FMM_ERR_INVALID_ARG = 1
+FMM_ERR_UNSUPPORTED = 6
 FMM_ERR_TIMEOUT = 7
 STATUS_NAMES = {0: "FMM_OK", 1: "FMM_ERR_INVALID_ARG", 2: "FMM_ERR_ALIGNMENT", 3: "FMM_ERR_SHAPE_MISMATCH",
                 4: "FMM_ERR_OOM", 5: "FMM_ERR_CUDA", 6: "FMM_ERR_UNSUPPORTED", 7: "FMM_ERR_TIMEOUT",

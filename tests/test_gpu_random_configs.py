@@ -1,0 +1,91 @@
+"""GPU parity over seeded random plan configurations: shape, depth, precision,
+odd-size mode, last-level fusion, leaf tile, alpha/beta and operand residence
+drawn together, on small-integer data, where every configuration must equal
+the int64 product of the definition (c_ij = sum_k a_ik b_kj, Sec. 3.3) bit for
+bit.
+
+Exactness: with entries in [-r, r] a level's sums S, T grow at most 4x, so a
+leaf product of depth d is bounded by (K / 2^d) r^2 16^d and the post-additions
+multiply that by at most 4^d; the draw keeps that bound below 2^24 (fp32's
+exact-integer range), and the split precisions hold |S|, |T| <= r 4^d exactly
+in their hi parts (bf16: 256, tf32: 2048, fp16 after power-of-two scaling).
+alpha, beta and C are powers of two and small integers, so alpha AB + beta C
+is exact too.  Configurations the library refuses (FMM_ERR_UNSUPPORTED) are
+counted, and most draws must run.
+"""
+import numpy as np
+import pytest
+
+import oracle.fmm_oracle as O
+from paper_1205_2927_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N_CONFIGS = 200
+
+
+def _draw(rng):
+    d = int(rng.integers(0, 4))
+    r = 2 if d <= 2 else 1
+    kmax = 1500 if d <= 2 else 300
+    # the exactness bound of the module docstring, with a margin
+    while d > 0 and kmax * r * r * 8 ** d * 4 ** d >= 2 ** 23:
+        kmax //= 2
+    lo = max(1, 8 << d) if d > 0 else 1
+    m = int(np.exp(rng.uniform(np.log(lo), np.log(1600))))
+    n = int(np.exp(rng.uniform(np.log(lo), np.log(1600))))
+    k = int(np.exp(rng.uniform(np.log(lo), np.log(max(lo + 1, kmax)))))
+    cfg = dict(depth=d, precision=str(rng.choice(["fp32", "fp32", "bf16x3", "fp16x3", "tf32"])),
+               odd=str(rng.choice(["pad", "peel", "tile", "auto"])), fuse_last=int(rng.choice([-1, 0, 1])),
+               leaf_tile=int(rng.choice([0, 128, 256, 512])))
+    host = bool(rng.random() < 0.2)
+    if host:
+        cfg["odd"] = str(rng.choice(["pad", "auto"]))
+        cfg["host_operands"] = 1
+        cfg["host_copy"] = str(rng.choice(["default", "engine", "sm"]))
+    alpha = float(rng.choice([1.0, -1.0, 2.0, 0.5]))
+    beta = float(rng.choice([0.0, 0.0, 1.0, -2.0]))
+    return m, k, n, r, cfg, alpha, beta, host
+
+
+def test_random_configurations_bit_exact():
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    rng = np.random.default_rng(I.seed_for(6, 0))
+    ran, refused, seen = 0, 0, []
+    for i in range(N_CONFIGS):
+        m, k, n, r, cfg, alpha, beta, host = _draw(rng)
+        A = I.small_int((m, k), I.seed_for(6, 1) + i, r=r)
+        B = I.small_int((k, n), I.seed_for(6, 2) + i, r=r)
+        C0 = I.small_int((m, n), I.seed_for(6, 3) + i, r=3)
+        ref = (alpha * O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
+               + beta * C0.astype(np.float64)).astype(np.float32)
+        try:
+            p = F.Plan(m, n, k, **cfg)
+        except F.FmmError as e:
+            if e.status == F.FMM_ERR_UNSUPPORTED:
+                refused += 1
+                continue
+            raise
+        if host:
+            tA, tB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+            tC = torch.from_numpy(C0.copy()).pin_memory()
+        else:
+            tA, tB, tC = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), torch.from_numpy(C0.copy()).cuda()
+        p(tA, tB, tC, alpha=alpha, beta=beta)
+        torch.cuda.synchronize()
+        status = p.device_status()
+        info = dict(p.info)
+        p.close()
+        got = tC.cpu().numpy()
+        where = (m, k, n, cfg, alpha, beta, info)
+        assert status == 0, where
+        assert np.array_equal(got, ref), (where, float(np.max(np.abs(got - ref))))
+        ran += 1
+        seen.append((cfg["depth"], cfg["precision"], info.get("odd"), info.get("fuse_last"), host))
+    print(f"random configurations: {ran} run bit-exact, {refused} refused as unsupported")
+    assert ran >= int(0.75 * N_CONFIGS), (ran, refused)
+    # the draw reached the paths it is meant to cross
+    assert {d for d, *_ in seen} >= {0, 1, 2, 3}
+    assert {p for _, p, *_ in seen} >= {"fp32", "bf16x3", "fp16x3", "tf32"}
+    assert any(h for *_, h in seen) and any(f for *_, f, _ in seen)
