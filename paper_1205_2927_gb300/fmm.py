@@ -128,6 +128,13 @@ def options(depth=-1, cutoff=2048, leaf_tile=0, precision="fp32", odd="auto", pl
     return o
 
 
+def _ld(t):
+    """Leading dimension (row stride, elements) of a 2-D row-major operand; an
+    empty operand is never read, so any valid value will do (numpy-backed empty
+    tensors carry stride 0)."""
+    return max(t.stride(0), 1) if t.numel() > 0 else max(t.shape[1], 1)
+
+
 def _stream_ptr(stream):
     import torch
     if stream is None:
@@ -201,13 +208,13 @@ def fmm_residual(A, B, Cm, x, fp64=False, stream=None):
     M, K = A.shape
     N = B.shape[1]
     need = C.c_size_t(0)
-    _check(_lib.fmm_residual(M, N, K, None, max(A.stride(0), 1), None, max(B.stride(0), 1), None,
-                             max(Cm.stride(0), 1), None, None, None, 0, C.byref(need), int(fp64), None),
+    _check(_lib.fmm_residual(M, N, K, None, _ld(A), None, _ld(B), None,
+                             _ld(Cm), None, None, None, 0, C.byref(need), int(fp64), None),
            "fmm_residual(query)")
     ws = torch.empty(max(need.value, 256), dtype=torch.uint8, device=A.device)
     r = torch.empty(M, dtype=torch.float64, device=A.device)
-    _check(_lib.fmm_residual(M, N, K, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
-                             Cm.data_ptr(), max(Cm.stride(0), 1), x.data_ptr(), r.data_ptr(), ws.data_ptr(),
+    _check(_lib.fmm_residual(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B),
+                             Cm.data_ptr(), _ld(Cm), x.data_ptr(), r.data_ptr(), ws.data_ptr(),
                              ws.numel(), C.byref(need), int(fp64), _stream_ptr(stream)), "fmm_residual")
     return r
 
@@ -240,8 +247,8 @@ def fmm_gemm_static(A, B, Cm, alpha=1.0, beta=0.0, stream=None):
     _check_static_operands(A, B, Cm)
     M, K = A.shape
     N = B.shape[1]
-    _check(_lib.fmm_gemm_static(M, N, K, float(alpha), A.data_ptr(), max(A.stride(0), 1), B.data_ptr(),
-                                max(B.stride(0), 1), float(beta), Cm.data_ptr(), max(Cm.stride(0), 1),
+    _check(_lib.fmm_gemm_static(M, N, K, float(alpha), A.data_ptr(), _ld(A), B.data_ptr(),
+                                _ld(B), float(beta), Cm.data_ptr(), _ld(Cm),
                                 _stream_ptr(stream)), "fmm_gemm_static")
     return Cm
 
@@ -340,7 +347,7 @@ def matmul(A, B, depth=-1, precision="fp32", **kw):
     """C = A @ B for contiguous float32 CUDA tensors via a one-off plan."""
     M, K = A.shape
     N = B.shape[1]
-    p = Plan(M, N, K, A.stride(0), B.stride(0), N, depth=depth, precision=precision, **kw)
+    p = Plan(M, N, K, _ld(A), _ld(B), N, depth=depth, precision=precision, **kw)
     return p(A, B)
 
 
@@ -382,9 +389,9 @@ class BatchedPlan:
         al = [alpha] * n if not isinstance(alpha, (list, tuple)) else alpha
         be = [beta] * n if not isinstance(beta, (list, tuple)) else beta
         self._arrs = (i64(*[a.shape[0] for a in As]), i64(*[b.shape[1] for b in Bs]), i64(*[a.shape[1] for a in As]),
-                      vp(*[a.data_ptr() for a in As]), i64(*[max(a.stride(0), 1) for a in As]),
-                      vp(*[b.data_ptr() for b in Bs]), i64(*[max(b.stride(0), 1) for b in Bs]),
-                      vp(*[c.data_ptr() for c in Cs]), i64(*[max(c.stride(0), 1) for c in Cs]),
+                      vp(*[a.data_ptr() for a in As]), i64(*[_ld(a) for a in As]),
+                      vp(*[b.data_ptr() for b in Bs]), i64(*[_ld(b) for b in Bs]),
+                      vp(*[c.data_ptr() for c in Cs]), i64(*[_ld(c) for c in Cs]),
                       f(*al), f(*be))
         self.opt = options(**opt_kwargs)
         need = C.c_size_t(0)
@@ -472,9 +479,9 @@ def fmm_gemm_batched(As, Bs, Cs, alpha=1.0, beta=0.0, stream=None, **opt_kwargs)
     al = [alpha] * n if not isinstance(alpha, (list, tuple)) else alpha
     be = [beta] * n if not isinstance(beta, (list, tuple)) else beta
     arrs = (i64(*[a.shape[0] for a in As]), i64(*[b.shape[1] for b in Bs]), i64(*[a.shape[1] for a in As]),
-            vp(*[a.data_ptr() for a in As]), i64(*[max(a.stride(0), 1) for a in As]),
-            vp(*[b.data_ptr() for b in Bs]), i64(*[max(b.stride(0), 1) for b in Bs]),
-            vp(*[c.data_ptr() for c in Cs]), i64(*[max(c.stride(0), 1) for c in Cs]), f(*al), f(*be))
+            vp(*[a.data_ptr() for a in As]), i64(*[_ld(a) for a in As]),
+            vp(*[b.data_ptr() for b in Bs]), i64(*[_ld(b) for b in Bs]),
+            vp(*[c.data_ptr() for c in Cs]), i64(*[_ld(c) for c in Cs]), f(*al), f(*be))
     opt = options(**opt_kwargs)
     need = C.c_size_t(0)
     _check(_lib.fmm_gemm_batched(n, *arrs, C.byref(opt), None, 0, C.byref(need), None), "fmm_gemm_batched(query)")

@@ -321,3 +321,14 @@ def test_auto_odd_mode_accepted_by_host_and_batched_plans(F):
     assert F.library().fmm_plan(None, 1000, 1000, 1000, 1000, 1000, 1000, C.byref(o), None, 0, C.byref(need), None) == 0
     o = F.options(odd="tile", host_operands=1, depth=1)
     assert F.library().fmm_plan(None, 1000, 1000, 1000, 1000, 1000, 1000, C.byref(o), None, 0, C.byref(need), None) == 6
+
+
+def test_leading_dimension_of_empty_operands(F):
+    # numpy-backed empty tensors carry stride 0; the binding passes a valid
+    # leading dimension for them (they are never read), so a K = 0 member of a
+    # batch is not refused for ld < N
+    import numpy as np
+    import torch
+    assert F._ld(torch.from_numpy(np.zeros((0, 7), np.float32))) == 7
+    assert F._ld(torch.from_numpy(np.zeros((5, 0), np.float32))) == 1
+    assert F._ld(torch.zeros((4, 6))[:, :3]) == 6

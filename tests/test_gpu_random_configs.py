@@ -89,3 +89,71 @@ def test_random_configurations_bit_exact():
     assert {d for d, *_ in seen} >= {0, 1, 2, 3}
     assert {p for _, p, *_ in seen} >= {"fp32", "bf16x3", "fp16x3", "tf32"}
     assert any(h for *_, h in seen) and any(f for *_, f, _ in seen)
+
+
+# per-term error bounds of the split forms against the FP32 bound (the same
+# derivation as the full-size tests: BF16x3 3 * 2^-16, TF32 2^-10 per term)
+SPLIT_BOUND = {"fp32": 2e-6, "fp16x3": 2e-6, "bf16x3": 4.8e-5, "tf32": 1.0e-3}
+
+
+def test_random_configurations_float_bound():
+    # float operands make every lo plane non-zero (integer data leaves lo = 0 in
+    # every split), so this draw checks the lo paths the exact test cannot
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    rng = np.random.default_rng(I.seed_for(6, 10))
+    worst = {}
+    for i in range(40):
+        m, k, n, _, cfg, _, _, host = _draw(rng)
+        k = max(k, int(rng.integers(64, 1600)))   # floats need no exactness bound on K
+        A, B = I.operands(m, k, n, I.seed_for(6, 11) + i, str(rng.choice(["normal", "loguniform"])))
+        p = F.Plan(m, n, k, **cfg)
+        if host:
+            tA, tB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+            tC = torch.full((m, n), float("nan")).pin_memory()
+        else:
+            tA, tB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+            tC = torch.full((m, n), float("nan"), device="cuda")
+        p(tA, tB, tC)
+        torch.cuda.synchronize()
+        assert p.device_status() == 0
+        p.close()
+        err = O.error_metric(tC.cpu().numpy(), O.classical(A, B), A, B)
+        prec = cfg["precision"]
+        worst[prec] = max(worst.get(prec, 0.0), err)
+        assert err <= SPLIT_BOUND[prec], (m, k, n, cfg, err)
+    print("worst error per precision:", {p: f"{e:.2e}" for p, e in worst.items()})
+
+
+def test_random_batched_sets_bit_exact():
+    # batched sets of random size and shape mix (including K = 0 and alpha = 0
+    # members), random precision, leaf tile and cut-off, per-problem alpha/beta
+    import torch
+    from paper_1205_2927_gb300 import fmm as F
+    rng = np.random.default_rng(I.seed_for(6, 20))
+    for t in range(8):
+        count = int(rng.integers(1, 40))
+        probs, al, be = [], [], []
+        for i in range(count):
+            m, n = (int(x) for x in rng.integers(1, 700, size=2))
+            k = 0 if rng.random() < 0.05 else int(rng.integers(1, 700))
+            A = I.small_int((m, k), I.seed_for(6, 21) + 100 * t + i, r=2)
+            B = I.small_int((k, n), I.seed_for(6, 22) + 100 * t + i, r=2)
+            C0 = I.small_int((m, n), I.seed_for(6, 23) + 100 * t + i, r=3)
+            probs.append((A, B, C0))
+            al.append(0.0 if rng.random() < 0.05 else float(rng.choice([1.0, -1.0, 2.0])))
+            be.append(float(rng.choice([0.0, 1.0, -0.5])))
+        prec = str(rng.choice(["fp32", "bf16x3", "fp16x3", "tf32"]))
+        tile = int(rng.choice([128, 256, 512])) if prec == "tf32" else int(rng.choice([256, 512]))
+        cutoff = int(rng.choice([128, 4096]))   # depth <= 2 below 700: intermediates stay exact
+        As = [torch.from_numpy(A).cuda() for A, _, _ in probs]
+        Bs = [torch.from_numpy(B).cuda() for _, B, _ in probs]
+        Cs = [torch.from_numpy(C0.copy()).cuda() for _, _, C0 in probs]
+        bp = F.BatchedPlan(As, Bs, Cs, alpha=al, beta=be, precision=prec, leaf_tile=tile, cutoff=cutoff)
+        bp.run()
+        torch.cuda.synchronize()
+        for (A, B, C0), a, b, Cd in zip(probs, al, be, Cs):
+            ref = (a * O.classical(A.astype(np.int64), B.astype(np.int64)).astype(np.float64)
+                   + b * C0.astype(np.float64)).astype(np.float32)
+            assert np.array_equal(Cd.cpu().numpy(), ref), (t, A.shape, B.shape, prec, tile, cutoff, a, b)
+        bp.close()
