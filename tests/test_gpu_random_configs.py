@@ -67,20 +67,35 @@ def test_random_configurations_bit_exact():
                 refused += 1
                 continue
             raise
+        pad = (0, 0, 0)
         if host:
             tA, tB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
             tC = torch.from_numpy(C0.copy()).pin_memory()
         else:
-            tA, tB, tC = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), torch.from_numpy(C0.copy()).cuda()
+            if rng.random() < 0.35:
+                # operands as views of wider buffers: row strides that need not
+                # be multiples of 4, NaN in the columns beyond each view
+                p.close()
+                pad = tuple(int(x) for x in rng.integers(1, 9, size=3))
+                p = F.Plan(m, n, k, lda=k + pad[0], ldb=n + pad[1], ldc=n + pad[2], **cfg)
+            fA = torch.full((m, k + pad[0]), float("nan"), device="cuda")
+            fB = torch.full((k, n + pad[1]), float("nan"), device="cuda")
+            fC = torch.full((m, n + pad[2]), float("nan"), device="cuda")
+            tA, tB, tC = fA[:, :k], fB[:, :n], fC[:, :n]
+            tA.copy_(torch.from_numpy(A))
+            tB.copy_(torch.from_numpy(B))
+            tC.copy_(torch.from_numpy(C0))
         p(tA, tB, tC, alpha=alpha, beta=beta)
         torch.cuda.synchronize()
         status = p.device_status()
         info = dict(p.info)
         p.close()
         got = tC.cpu().numpy()
-        where = (m, k, n, cfg, alpha, beta, info)
+        where = (m, k, n, pad, cfg, alpha, beta, info)
         assert status == 0, where
         assert np.array_equal(got, ref), (where, float(np.max(np.abs(got - ref))))
+        if not host:
+            assert torch.isnan(fC[:, n:]).all(), where    # nothing written beyond C
         ran += 1
         seen.append((cfg["depth"], cfg["precision"], info.get("odd"), info.get("fuse_last"), host))
     print(f"random configurations: {ran} run bit-exact, {refused} refused as unsupported")
