@@ -796,14 +796,32 @@ def main():
     split = None
     if args.precision == "fp32" and not args.no_split:
         split = {"depth": depth, "bound": 2e-6}
+        # the 16-bit leaves' roofline: kind::f16 work of the leaf launch against the
+        # project's tcgen05 probe in the same instruction shape (bf16 operands)
+        probe16 = tensor_peak(fmm, local, "bf16")
+        split["peak_bf16_probe_tflops"] = round(probe16["tflops"], 1)
+        leaf_side = ((n + (4 << depth) - 1) // (4 << depth) * (4 << depth)) >> depth if depth > 0 else n
+        leaf_work16 = 3 * 2.0 * 7 ** depth * float(leaf_side) ** 3
         dC2 = torch.empty((n, n), device="cuda")
         for prec in ("fp16x3", "bf16x3"):
             sp = fmm.Plan(n, n, n, depth=depth, precision=prec, leaf_tile=args.leaf_tile)
             sms = timed(torch, dist, world, lambda: sp(dA, dB, dC2), min(args.steps, 10), 3)
             assert sp.device_status() == 0, "device status word set"
+            # phase split from a few more calls with the plan's CUDA-event marks
+            sp.profile(True)
+            for _ in range(3):
+                sp(dA, dB, dC2)
+            torch.cuda.synchronize()
+            pr = sp.profile_read()
             sp.close()
+            calls = max(pr["calls"], 1)
+            leaf16_ms = pr["leaf_ms"] / calls
             entry = {"gflops": round(flops * world / sms / 1e6, 1), "ms_per_step": round(sms, 3),
-                     "error": sampled_error(np, torch, dC2, A_h, B_h)}
+                     "error": sampled_error(np, torch, dC2, A_h, B_h),
+                     "phases": {"pre_add_ms": round(pr["pre_ms"] / calls, 3), "leaf_ms": round(leaf16_ms, 3),
+                                "post_add_ms": round(pr["post_ms"] / calls, 3)},
+                     "leaf_tflops": round(leaf_work16 / (leaf16_ms * 1e-3) / 1e12, 1),
+                     "leaf_frac_of_bf16_probe": round(leaf_work16 / (leaf16_ms * 1e-3) / 1e12 / probe16["tflops"], 3)}
             if classical:
                 sc = fmm.Plan(n, n, n, depth=0, precision=prec, leaf_tile=args.leaf_tile)
                 scms = timed(torch, dist, world, lambda: sc(dA, dB, dC2), min(args.steps, 10), 3)
