@@ -330,7 +330,7 @@ def wl_sweep(args):
             pA, pB = torch.from_numpy(A_h).pin_memory(), torch.from_numpy(B_h).pin_memory()
             pC = torch.empty((n, n)).pin_memory()
             for d in range(0, 5):
-                for odd in (("pad", "peel") if n == 19000 and d > 0 else ("pad",)):
+                for odd in (("pad", "peel", "auto") if n == 19000 and d > 0 else ("pad",)):
                     p = fmm.Plan(n, n, n, depth=d, odd=odd)
                     ms = event_ms(torch, lambda: p(dA, dB, dC), 3, 2)
                     err = sampled_error(np, torch, dC, A_h, B_h)

@@ -116,7 +116,8 @@ typedef struct {
                                   pass) and never stored.  Applies to depth-2 to depth-4 plans
                                   on CTA-pair tiles with split-plane leaves (FP32, BF16X3,
                                   FP16X3; device operands).  1 on, -1 off, 0 library default
-                                  (on at depths 2 and 3, off at depth 4) */
+                                  (on at depths 2 and 3 when every leaf is whole 256 x 256
+                                  tiles in M and N, off otherwise and at depth 4) */
     int host_copy;             /* host-resident plans: how A, B, C cross the host link.
                                   1: copy engines (cudaMemcpy2DAsync); 2: SM loads and stores
                                   on the device mapping of the pinned memory (32 blocks; the

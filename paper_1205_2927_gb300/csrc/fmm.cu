@@ -1311,10 +1311,25 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
     // the fused last level needs the CTA-pair kernel on split planes and a
     // Winograd depth of 2 to 4 (the node outputs then fold into C in one pass)
     const bool fusable = t.pair && t.pre16 && !t.host && t.rmul == 0 && t.depth >= 2 && t.depth <= 4;
-    // by default at depths 2 and 3 (n = 16384, depth 3: 0.4-0.5 ms faster per
-    // call); at depth 4 on request (n = 32768: post-additions 8.8 -> 4.8 ms but
-    // the call measured slower, 172-182 against 163-165 ms)
-    t.fused = fusable && (o.fuse_last > 0 || (o.fuse_last == 0 && kFuseLastDefault && t.depth <= 3)) ? 1 : 0;
+    // by default at depths 2 and 3 where every leaf is whole 256 x 256 pair tiles
+    // in M and N (n = 16384, depth 3: 0.4-0.6 ms faster per call); with ragged
+    // leaves a unit's seven products run as one, so its edge tiles and the
+    // launch's last partial wave of units cost more than the post pass saves
+    // (n = 19000, leaves 2376 wide: 0.3-1.9 ms slower at depth 3, 0.2-0.9 ms at
+    // depth 2); at depth 4 on request (n = 32768: post-additions 8.8 -> 4.8 ms
+    // but the call measured slower, 172-182 against 163-165 ms)
+    bool whole = false;
+    if (t.depth > 0) {
+        const long long g = 4LL << t.depth;
+        auto leaf_side = [&](long long X, long long gx) {
+            const long long gg = gx ? gx : g;
+            return (t.peel ? X / gg * gg : (X + g - 1) / g * g) >> t.depth;
+        };
+        whole = leaf_side(M, t.peel_gm) % 256 == 0 && leaf_side(N, t.peel_gn) % 256 == 0;
+    }
+    t.fused = fusable && (o.fuse_last > 0 || (o.fuse_last == 0 && kFuseLastDefault && t.depth <= 3 && whole))
+                  ? 1
+                  : 0;
 }
 
 size_t plan_bytes(long long M, long long N, long long K, long long lda, long long ldb, long long ldc,

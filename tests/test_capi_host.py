@@ -227,6 +227,13 @@ def test_fused_workspace_closed_forms(F, n, d, prec, es):
     default = _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512, odd="pad")
     assert default == (need if d <= 3 else _query(F, n, n, n, depth=d, precision=prec, leaf_tile=512,
                                                   fuse_last=-1, odd="pad"))
+    # by default only where the leaves are whole 256 x 256 tiles: n = 19000
+    # (leaves 2376 wide at depth 3, 4752 at depth 2) stays unfused
+    for dd in (2, 3):
+        assert _query(F, 19000, 19000, 19000, depth=dd, precision=prec, leaf_tile=512, odd="pad") == \
+            _query(F, 19000, 19000, 19000, depth=dd, precision=prec, leaf_tile=512, fuse_last=-1, odd="pad")
+        assert _query(F, 19000, 19000, 19000, depth=dd, precision=prec, leaf_tile=512, fuse_last=1, odd="pad") != \
+            _query(F, 19000, 19000, 19000, depth=dd, precision=prec, leaf_tile=512, fuse_last=-1, odd="pad")
     # options a fused plan cannot take fall back to the unfused schedule
     assert _query(F, n, n, n, depth=1, precision=prec, leaf_tile=512, fuse_last=1) == \
         _query(F, n, n, n, depth=1, precision=prec, leaf_tile=512, fuse_last=-1)
