@@ -72,9 +72,9 @@ typedef enum {
                          multiple of (leaf tile x 2^depth) in M and N (256 x 2^depth for CTA
                          pairs), so every leaf is a whole number of tiles; the border rows and
                          columns (and K's remainder modulo 4 x 2^depth) run as classical leaves */
-    FMM_ODD_AUTO = 3  /* TILE when each of M and N leaves a remainder of at most a quarter
-                         (depth >= 3) or an eighth (depth 1-2) of its whole-tile granule, and
-                         some remainder; else PAD.  Host-resident and batched plans pad.
+    FMM_ODD_AUTO = 3  /* TILE when each of M and N leaves a remainder of at most an eighth
+                         of its whole-tile granule, and some remainder; else PAD.
+                         Host-resident and batched plans pad.
                          fmm_plan_info reports the mode taken */
 } fmm_odd_t;
 

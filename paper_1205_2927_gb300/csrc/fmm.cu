@@ -1260,11 +1260,11 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
         t.depth = 0;
     }
     // odd sizes: AUTO peels to whole leaf tiles when every peeled dimension's
-    // remainder is small against its granule (the last tile row or column of
-    // every leaf would be mostly padding) and pads otherwise: at most a quarter
-    // of the granule at depth >= 3, an eighth below (n = 4096 .. 20480, same-GPU
-    // sweeps: every eighth-granule case gained 4-17 %; quarter-granule cases
-    // gained in 5 of 6 at depth 3 and were mixed at depth 2); host-resident
+    // remainder is at most an eighth of its granule (the last tile row or
+    // column of every leaf would be mostly padding) and pads otherwise.  Same-GPU
+    // sweeps over n = 4352 .. 19712 against padded plans (the last level unfused
+    // on their ragged leaves): every eighth-granule case gained (+0.8 to +12.5 %
+    // at depth 3), quarter-granule ones were mixed (-5.2 to +3.3 %).  Host-resident
     // plans always pad
     fmm_odd_t odd = o.odd;
     const long long tm = (bn == 512) ? 256 : kBM, tn = (bn == 512) ? 256 : bn;
@@ -1273,8 +1273,7 @@ void make_tmp(fmm_plan_s& t, long long M, long long N, long long K, long long ld
         if (!t.host && t.depth > 0 && o.algo == FMM_ALGO_WINOGRAD) {
             const long long gm = tm << t.depth, gn = tn << t.depth;
             const long long rm = M % gm, rn = N % gn;
-            const long long q = t.depth >= 3 ? 4 : 8;   // remainder limit: granule / q
-            if (M >= gm && N >= gn && (rm > 0 || rn > 0) && q * rm <= gm && q * rn <= gn) odd = FMM_ODD_TILE;
+            if (M >= gm && N >= gn && (rm > 0 || rn > 0) && 8 * rm <= gm && 8 * rn <= gn) odd = FMM_ODD_TILE;
         }
     }
     t.odd = odd;

@@ -312,10 +312,11 @@ def test_tile_peel_workspace_covers_only_the_whole_tile_core(F):
     assert tile < pad + border
 
 
-@pytest.mark.parametrize("n,d,resolved", [(16640, 3, "tile"), (16896, 3, "tile"), (19000, 3, "pad"),
-                                          (20224, 2, "pad"), (16384, 3, "pad"), (18688, 3, "tile")])
+@pytest.mark.parametrize("n,d,resolved", [(16640, 3, "tile"), (16896, 3, "pad"), (19000, 3, "pad"),
+                                          (20224, 2, "pad"), (16384, 3, "pad"), (18688, 3, "tile"),
+                                          (8448, 3, "tile"), (10752, 3, "pad"), (9344, 2, "tile")])
 def test_auto_odd_mode_resolution(F, n, d, resolved):
-    # AUTO peels to whole leaf tiles when each remainder is at most a quarter of
+    # AUTO peels to whole leaf tiles when each remainder is at most an eighth of
     # the granule (256 * 2^d on CTA pairs), else pads: its workspace is that mode's
     auto = _query(F, n, n, n, depth=d, leaf_tile=512, odd="auto")
     want = _query(F, n, n, n, depth=d, leaf_tile=512, odd=resolved)
